@@ -1,0 +1,35 @@
+"""The flop model reproduces the FLOP columns of Tables 2 and 3 exactly."""
+
+import os
+
+from oracle import flops
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables_2_3_flop.txt")
+
+
+def load():
+    rows = []
+    with open(GOLDEN) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            size, t2, t3 = line.split()
+            rows.append((tuple(int(v) for v in size.split("x")), int(t2), int(t3)))
+    return rows
+
+
+def test_tables_2_and_3():
+    rows = load()
+    assert len(rows) == 5
+    for block, t2, t3 in rows:
+        assert flops.table2_flop(block) == t2
+        assert flops.table3_flop(block) == t3
+
+
+def test_per_site_counts():
+    # 4^4 domains, n_sap = 4, n_jac = 4, chiral basis (168 flop for every hop)
+    h = (168, 168, 168, 168)
+    assert flops.f_in((4, 4, 4, 4), h) == 1608
+    assert flops.f_out((4, 4, 4, 4), h) * 2 == 1797
+    assert flops.D_FLOP_PER_SITE == 1320 + 504
