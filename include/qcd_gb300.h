@@ -1,0 +1,249 @@
+/*
+ * qcd_gb300.h -- C ABI of the Clover-Wilson SAP-BiCGStab quark solver for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The library implements the quark solver of arXiv:2109.10687:
+ *   D = 1 + C - kappa H                          (App. A)
+ *   A = C_inv D = I - kappa C_inv H              (Sec. 3, Eq. hoppingmat)
+ * preconditioned by the red/black Schwarz alternating procedure with Jacobi
+ * domain inverses (Sec. 3, Eq. Msap, Algorithms 1-3), solved by BiCGStab
+ * (Algorithm 5) inside a float64 defect-correction loop (Algorithm 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns an int status (QCD_OK = 0 on success).  No C++
+ *   exception crosses this boundary.  qcd_last_error() gives a message for
+ *   the last failing call on a context.
+ * - dims[4] = {Lx, Ly, Lz, Lt}; domain[4] = {dx, dy, dz, dt}.  Every d_mu is a
+ *   power of two, dx*dy*dz*dt <= 256, and every L_mu is a multiple of 2*d_mu
+ *   (an even number of domains per direction keeps the red/black colouring
+ *   of Sec. 3 consistent across the periodic boundary).  Default domain 4^4.
+ * - Boundary conditions: periodic in x, y, z; bc_t = +1 (periodic) or -1
+ *   (antiperiodic) in t, applied as a sign on every hop across t = Lt-1 <-> 0.
+ * - CANONICAL layout (host or device, float64, little endian, x fastest):
+ *     quark field : [t][z][y][x][colour 3][spin 4][re, im]        (Sec. 4, "K")
+ *     gauge field : [t][z][y][x][mu 4 = x,y,z,t][row 3][col 3][re, im]
+ *   With nrhs > 1 right-hand sides the quark fields are stacked: [rhs][...].
+ * - Gamma basis of canonical quark fields: QCD_BASIS_CHIRAL (default;
+ *   gamma_5 = diag(1,1,-1,-1)) or QCD_BASIS_PAPER (the matrices printed in
+ *   App. A).  Kernels always work in the chiral basis; paper-basis fields are
+ *   rotated on import and export.
+ * - INTERNAL layout: the device-resident, domain-blocked structure of arrays
+ *   used by the kernels.  Its size comes from qcd_field_bytes(); the caller
+ *   allocates such buffers (cudaMalloc, torch, ...) and owns them; the
+ *   library only reads and writes them on the given stream.  Fields move
+ *   between the two layouts with qcd_import_spinor / qcd_export_spinor.
+ * - Precision codes: QCD_PREC_DOUBLE (float64 storage and arithmetic),
+ *   QCD_PREC_SINGLE (float32), QCD_PREC_HALF (float16 storage with a float32
+ *   norm per site; float32 arithmetic).
+ * - stream: a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *   Calls that return host-visible results (qcd_solve, qcd_norm2, ...)
+ *   synchronise that stream before returning.
+ * - The library owns its copies of U, the clover term and its workspaces
+ *   (device memory it allocates on first use and frees in qcd_destroy).
+ * - A context is not thread safe; use one context per host thread.
+ */
+#ifndef QCD_GB300_H
+#define QCD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum qcd_status {
+  QCD_OK = 0,
+  QCD_ERR_ARG = 1,            /* invalid argument or unsupported size       */
+  QCD_ERR_CUDA = 2,           /* a CUDA runtime call failed                 */
+  QCD_ERR_OOM = 3,            /* device allocation failed                   */
+  QCD_ERR_NOT_CONVERGED = 4,  /* iteration limit reached before tolerance   */
+  QCD_ERR_BREAKDOWN = 5,      /* BiCGStab breakdown (rho, <r~|q> or |t|^2=0) */
+  QCD_ERR_NONFINITE = 6,      /* NaN or Inf met in a residual              */
+  QCD_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up         */
+  QCD_ERR_STATE = 8           /* call out of order (no gauge field, ...)    */
+};
+
+enum qcd_precision { QCD_PREC_DOUBLE = 0, QCD_PREC_SINGLE = 1, QCD_PREC_HALF = 2 };
+enum qcd_basis { QCD_BASIS_CHIRAL = 0, QCD_BASIS_PAPER = 1 };
+
+typedef struct qcd_ctx qcd_ctx;
+
+/* Parameters of qcd_solve (Algorithms 4 and 5). */
+typedef struct qcd_solve_params {
+  double tol;          /* outer stop: |b - D x| / |b| < tol, float64 (Alg. 4)  */
+  double inner_tol;    /* inner stop of Algorithm 5 on the preconditioned
+                          system, relative to its right-hand side            */
+  int max_outer;       /* defect-correction steps (Alg. 4), e.g. 20          */
+  int max_inner;       /* BiCGStab iterations per inner solve (Alg. 5)      */
+  int n_sap;           /* loop count of Algorithm 1 (K applied n_sap+1 times) */
+  int n_jac;           /* A_EE applications in Algorithm 2 (>= 1)            */
+  int sap_prec;        /* QCD_PREC_SINGLE or QCD_PREC_HALF storage for SAP   */
+  int use_graph;       /* 1: replay each BiCGStab iteration as a CUDA graph  */
+  int x_is_guess;      /* 1: x holds an initial guess on entry (resume)      */
+} qcd_solve_params;
+
+/* Results of qcd_solve, one entry per right-hand side where indicated. */
+typedef struct qcd_solve_info {
+  int outer_iters;         /* defect-correction steps taken                */
+  int inner_iters;         /* BiCGStab iterations summed over outer steps  */
+  int status;              /* qcd_status of the solve                      */
+  double true_resid;       /* largest final |b - D x| / |b| over the rhs   */
+  double seconds;          /* wall time inside qcd_solve                   */
+} qcd_solve_info;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context for one lattice on the current CUDA device.
+ * dims, domain: see above (domain may be NULL for 4^4).  bc_t: +1 or -1.
+ * basis: QCD_BASIS_CHIRAL or QCD_BASIS_PAPER for canonical quark fields.
+ * Errors: QCD_ERR_ARG (bad sizes), QCD_ERR_CUDA, QCD_ERR_OOM. */
+int qcd_create(const int dims[4], const int domain[4], int bc_t, int basis, qcd_ctx** out);
+
+/* Free every device buffer the context owns, then the context. */
+int qcd_destroy(qcd_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last qcd_create when
+ * ctx is NULL).  The string is owned by the library. */
+const char* qcd_last_error(const qcd_ctx* ctx);
+
+/* Library version string, e.g. "qcd_gb300 1.0". */
+const char* qcd_version(void);
+
+/* ---- gauge field and clover term -------------------------------------- */
+
+/* Copy the gauge field U (canonical layout, float64, 4 V 9 complex) into the
+ * context in float64, float32 and float16 internal layouts.  U_mu(n) is the
+ * SU(3) link from n to n + mu (App. A; U_{-mu}(n) = U_mu(n - mu)^dag).
+ * on_device: 1 if U is a device pointer, 0 for host memory.
+ * check_tol > 0: reject links with |U^dag U - 1| or |det U - 1| above it
+ * (QCD_ERR_ARG).  Invalidates a previously built clover term. */
+int qcd_set_gauge(qcd_ctx* ctx, const double* U, int on_device, double check_tol, void* stream);
+
+/* Set the hopping parameter kappa and the clover coefficient c_SW (App. A).
+ * Invalidates a previously built clover term. */
+int qcd_set_params(qcd_ctx* ctx, double kappa, double csw);
+
+/* Build the clover term of App. A from the four-leaf field strength
+ *   F_mu,nu = (Q_mu,nu - Q_mu,nu^dag) / 8,
+ *   C = i kappa c_SW sum_{mu<nu} sigma_mu,nu F_mu,nu,
+ * as two 6x6 Hermitian chiral blocks per site, and C_inv = (1 + C)^-1
+ * (float64 arithmetic; float64, float32 and float16 copies are kept).
+ * Errors: QCD_ERR_STATE without a gauge field; QCD_ERR_NONFINITE if a block
+ * is singular. */
+int qcd_build_clover(qcd_ctx* ctx, void* stream);
+
+/* ---- fields ----------------------------------------------------------- */
+
+/* Bytes of one internal quark field of the given precision times nrhs. */
+int qcd_field_bytes(const qcd_ctx* ctx, int prec, int nrhs, size_t* bytes);
+
+/* Canonical float64 (host or device) -> internal layout of precision prec. */
+int qcd_import_spinor(qcd_ctx* ctx, void* dst, const double* src, int prec, int nrhs,
+                      int src_on_device, void* stream);
+
+/* Internal layout of precision prec -> canonical float64 (host or device). */
+int qcd_export_spinor(qcd_ctx* ctx, double* dst, const void* src, int prec, int nrhs,
+                      int dst_on_device, void* stream);
+
+/* ---- operators (all on internal-layout device buffers) ---------------- */
+
+/* out = D in (dagger = 0) or D^dag in = gamma_5 D gamma_5 in (dagger = 1),
+ * D x = (1 + C) x - kappa sum_mu [(1 - g_mu) U_mu(n) x(n+mu)
+ *                                + (1 + g_mu) U_mu(n-mu)^dag x(n-mu)]   (App. A).
+ * prec: QCD_PREC_DOUBLE or QCD_PREC_SINGLE.  out and in must not alias. */
+int qcd_apply_D(qcd_ctx* ctx, void* out, const void* in, int prec, int dagger, int nrhs,
+                void* stream);
+
+/* out = A in = in - kappa C_inv H in (Sec. 3, Eq. hoppingmat); float32. */
+int qcd_apply_A(qcd_ctx* ctx, void* out, const void* in, int nrhs, void* stream);
+
+/* out = (1 + C) in (inverse = 0) or C_inv in (inverse = 1); prec DOUBLE or
+ * SINGLE.  out may alias in. */
+int qcd_apply_clover(qcd_ctx* ctx, void* out, const void* in, int prec, int inverse, int nrhs,
+                     void* stream);
+
+/* One block of A restricted to a domain colour (Sec. 3): row, col in {0 = E,
+ * 1 = O}.  out (all sites) = A_rc in: sites of colour row receive the
+ * result, the others are set to zero.  float32; test and diagnostic use. */
+int qcd_apply_A_block(qcd_ctx* ctx, void* out, const void* in, int row, int col, void* stream);
+
+/* x = M_SAP b (with_A = 0, Algorithm 1) or x = A M_SAP b (with_A = 1,
+ * Algorithm 3) on float32 internal fields; the sweeps store their vectors
+ * in float32 (sap_prec = QCD_PREC_SINGLE) or float16 (QCD_PREC_HALF).
+ * n_sap >= 0 is the loop count of Algorithm 1; n_jac >= 1 the number of
+ * A_EE applications of Algorithm 2.  out and in must not alias. */
+int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac, int sap_prec,
+                  int with_A, void* stream);
+
+/* ---- BLAS-1 (float32 internal fields, float64 results) --------------- */
+
+/* *result = |a|^2 (host pointer), accumulated per block in float32 and
+ * across blocks in float64, in a fixed order (deterministic). */
+int qcd_norm2(qcd_ctx* ctx, double* result, const void* a, int prec, int nrhs, void* stream);
+
+/* result[0] + i result[1] = <a|b> = a^dag b (host pointer). */
+int qcd_cdot(qcd_ctx* ctx, double result[2], const void* a, const void* b, int prec, int nrhs,
+             void* stream);
+
+/* ---- solver ----------------------------------------------------------- */
+
+/* Solve D x = b for nrhs right-hand sides (canonical float64 fields, host
+ * memory when on_device = 0, device memory when 1).  Algorithm 4 in float64
+ * around Algorithm 5 in float32 on (A M_SAP) y = C_inv r / |r|, the SAP
+ * preconditioner in float32 or float16 storage.  With nrhs > 1 all right-hand
+ * sides advance together and share every gauge-field and clover load.
+ * Returns QCD_OK when every rhs reached tol, QCD_ERR_NOT_CONVERGED,
+ * QCD_ERR_BREAKDOWN or QCD_ERR_NONFINITE otherwise (x then holds the last
+ * iterate).  info may be NULL. */
+int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int on_device,
+              const qcd_solve_params* params, qcd_solve_info* info, void* stream);
+
+/* Fill params with defaults: tol 1e-10, inner_tol 1e-6, max_outer 20,
+ * max_inner 500, n_sap 4, n_jac 4, sap_prec SINGLE, use_graph 0. */
+int qcd_solve_params_default(qcd_solve_params* params);
+
+/* ---- gradients -------------------------------------------------------- */
+
+/* Gradient of L = Re(eta^dag D^-1 b) (canonical float64 fields on the
+ * device):
+ *   grad_b = D^-dag eta = gamma_5 D^-1 gamma_5 eta            (solve),
+ *   grad_U[n][mu] = G_mu(n), with dL = sum Re tr(G^dag dU), from the
+ *   hopping term (outer products of x = D^-1 b and lambda = grad_b) and the
+ *   clover leaves; with project = 1 grad_U holds TA(G U^dag) instead, the
+ *   su(3) projection (traceless anti-Hermitian part).
+ * x and lam may be supplied (non-NULL, canonical float64 device fields) to
+ * skip the two solves; otherwise they are solved with params.
+ * grad_U layout: canonical gauge layout. */
+int qcd_grad(qcd_ctx* ctx, const double* eta, const double* b, const double* x,
+             const double* lam, double* grad_b, double* grad_U, int project,
+             const qcd_solve_params* params, void* stream);
+
+/* ---- instrumentation -------------------------------------------------- */
+
+enum qcd_kernel_class {
+  QCD_KC_DSLASH = 0,     /* D / D^dag / A applies                      */
+  QCD_KC_SAP_BLOCK = 1,  /* SAP domain kernels (Algorithms 1-3)        */
+  QCD_KC_BLAS = 2,       /* fused BLAS-1 and reductions                */
+  QCD_KC_DOUBLE = 3,     /* float64 operator and defect correction    */
+  QCD_KC_OTHER = 4,
+  QCD_KC_COUNT = 5
+};
+
+/* enable = 1: bracket every kernel launch with CUDA events on its stream
+ * and accumulate per-class device time; 0: stop (the default). */
+int qcd_profile_enable(qcd_ctx* ctx, int enable);
+
+/* Per class: launches and summed device milliseconds since the last reset
+ * (synchronises the events).  reset = 1 clears the counters afterwards. */
+int qcd_profile_read(qcd_ctx* ctx, int kernel_class, long long* launches, double* ms, int reset);
+
+/* Number of kernels the library has launched on this context so far. */
+int qcd_launch_count(const qcd_ctx* ctx, long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCD_GB300_H */

@@ -1,0 +1,272 @@
+// Clover-Wilson operator kernels: D, D^dag, A = C_inv D, the clover
+// multiply and the domain blocks A_EE / A_EO of Sec. 3 (arXiv:2109.10687,
+// App. A for D; Sec. 3 Eq. hoppingmat for A).
+//
+// One thread per site.  Each of the eight hops is spin-projected to a half
+// spinor (two spin rows), multiplied by the link (or its adjoint) and
+// rebuilt into the accumulator: 168 flop per hop, 1320 for the hopping term,
+// plus the clover block multiply.
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+template <typename R>
+struct Prec;
+template <>
+struct Prec<float> {
+  using SIO = F32Spinor;
+  using LP = LinkPtr<float>;
+  using CP = CloverPtrF32;
+  using CB = CloverBlockF32;
+};
+template <>
+struct Prec<double> {
+  using SIO = F64Spinor;
+  using LP = LinkPtr<double>;
+  using CP = CloverPtrF64;
+  using CB = CloverBlockF64;
+};
+
+// acc += hop in direction MU (both orientations); PMF / PMB are the projector
+// signs of the forward and backward hop.  FILTER: 0 all hops, 1 only hops
+// inside the domain, 2 only hops that leave the domain.
+template <int MU, int PMF, int PMB, int FILTER, typename R, typename SIO, typename LP>
+__device__ __forceinline__ void hop_dir(const Geom& g, const SIO& in, const LP& U, int dom, int s, int rhs_off,
+                                        Spinor<R>& acc) {
+  {
+    const bool intra = hop_is_intra(g, s, MU, true);
+    if (FILTER == 0 || (FILTER == 1 && intra) || (FILTER == 2 && !intra)) {
+      int nd, ns;
+      const int sign = nbr_site(g, dom, s, MU, true, nd, ns);
+      Spinor<R> p;
+      in.load(g, nd + rhs_off, ns, p);
+      HalfSpinor<R> h, uh;
+      project<MU, PMF>(p, h);
+      SU3<R> u;
+      U.load(g, dom, MU, s, u);
+      su3_mul(u, h, uh);
+      if (sign < 0) scale_half(uh, R(-1));
+      accumulate<MU, PMF>(acc, uh);
+    }
+  }
+  {
+    const bool intra = hop_is_intra(g, s, MU, false);
+    if (FILTER == 0 || (FILTER == 1 && intra) || (FILTER == 2 && !intra)) {
+      int nd, ns;
+      const int sign = nbr_site(g, dom, s, MU, false, nd, ns);
+      Spinor<R> p;
+      in.load(g, nd + rhs_off, ns, p);
+      HalfSpinor<R> h, uh;
+      project<MU, PMB>(p, h);
+      SU3<R> u;
+      U.load(g, nd, MU, ns, u);
+      su3_dag_mul(u, h, uh);
+      if (sign < 0) scale_half(uh, R(-1));
+      accumulate<MU, PMB>(acc, uh);
+    }
+  }
+}
+
+template <int PMF, int PMB, int FILTER, typename R, typename SIO, typename LP>
+__device__ __forceinline__ void hopping(const Geom& g, const SIO& in, const LP& U, int dom, int s, int rhs_off,
+                                        Spinor<R>& acc) {
+  zero(acc);
+  hop_dir<0, PMF, PMB, FILTER>(g, in, U, dom, s, rhs_off, acc);
+  hop_dir<1, PMF, PMB, FILTER>(g, in, U, dom, s, rhs_off, acc);
+  hop_dir<2, PMF, PMB, FILTER>(g, in, U, dom, s, rhs_off, acc);
+  hop_dir<3, PMF, PMB, FILTER>(g, in, U, dom, s, rhs_off, acc);
+}
+
+// D:    out = (1 + C) x - kappa H x
+// D^dag: out = (1 + C) x - kappa H^dag x   (gamma_5 H gamma_5 swaps the projectors)
+// A:    out = x - kappa C_inv H x
+template <typename R, int MODE>
+__global__ void __launch_bounds__(128) dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in,
+                                                     typename Prec<R>::LP U, typename Prec<R>::CP clov, R kappa) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int dom = (int)(gid >> g.logvd);
+  const int s = (int)(gid & (g.vd - 1));
+  const int rhs_off = blockIdx.y * g.ndom;
+  Spinor<R> acc;
+  if (MODE == MODE_DDAG) hopping<+1, -1, 0>(g, in, U, dom, s, rhs_off, acc);
+  else hopping<-1, +1, 0>(g, in, U, dom, s, rhs_off, acc);
+  Spinor<R> x;
+  in.load(g, dom + rhs_off, s, x);
+  if (MODE == MODE_A) {
+    clover_mul<R, typename Prec<R>::CP, typename Prec<R>::CB>(clov, g, dom, s, acc);
+  } else {
+    clover_mul<R, typename Prec<R>::CP, typename Prec<R>::CB>(clov, g, dom, s, x);
+  }
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x.v[sp][c].re = fma(-kappa, acc.v[sp][c].re, x.v[sp][c].re);
+      x.v[sp][c].im = fma(-kappa, acc.v[sp][c].im, x.v[sp][c].im);
+    }
+  out.store(g, dom + rhs_off, s, x);
+}
+
+template <typename R>
+__global__ void clover_apply_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in,
+                                    typename Prec<R>::CP clov) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int dom = (int)(gid >> g.logvd);
+  const int s = (int)(gid & (g.vd - 1));
+  const int rhs_off = blockIdx.y * g.ndom;
+  Spinor<R> x;
+  in.load(g, dom + rhs_off, s, x);
+  clover_mul<R, typename Prec<R>::CP, typename Prec<R>::CB>(clov, g, dom, s, x);
+  out.store(g, dom + rhs_off, s, x);
+}
+
+// A_rc of Sec. 3: rows of colour `row`, columns of colour `col`.
+__global__ void __launch_bounds__(128) ablock_kernel(Geom g, F32Spinor out, F32Spinor in, LinkPtr<float> U,
+                                                     CloverPtrF32 cinv, float kappa, int row, int col) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int dom = (int)(gid >> g.logvd);
+  const int s = (int)(gid & (g.vd - 1));
+  const int colour = dom >= g.nhalf;
+  Spinor<float> res;
+  zero(res);
+  if (colour == row) {
+    Spinor<float> acc;
+    if (row == col) hopping<-1, +1, 1>(g, in, U, dom, s, 0, acc);
+    else hopping<-1, +1, 2>(g, in, U, dom, s, 0, acc);
+    clover_mul<float, CloverPtrF32, CloverBlockF32>(cinv, g, dom, s, acc);
+    if (row == col) in.load(g, dom, s, res);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        res.v[sp][c].re = fmaf(-kappa, acc.v[sp][c].re, res.v[sp][c].re);
+        res.v[sp][c].im = fmaf(-kappa, acc.v[sp][c].im, res.v[sp][c].im);
+      }
+  }
+  out.store(g, dom, s, res);
+}
+
+void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st) {
+  const Geom& g = ctx->geom;
+  const int block = 128;
+  dim3 grid(grid_for(g.vol, block), nrhs);
+  if (prec == QCD_PREC_DOUBLE) {
+    QCD_REQUIRE(mode != MODE_A, QCD_ERR_ARG, "A is provided in float32 only");
+    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+    F64Spinor o{(double2*)out}, i{(double2*)in};
+    LinkPtr<double> U{ctx->u64};
+    CloverPtrF64 c{ctx->clov64};
+    if (mode == MODE_D) dslash_kernel<double, MODE_D><<<grid, block, 0, st>>>(g, o, i, U, c, ctx->kappa);
+    else dslash_kernel<double, MODE_DDAG><<<grid, block, 0, st>>>(g, o, i, U, c, ctx->kappa);
+    check_launch();
+  } else if (prec == QCD_PREC_SINGLE) {
+    LaunchScope ls(ctx, QCD_KC_DSLASH, st);
+    F32Spinor o{(float4*)out}, i{(float4*)in};
+    LinkPtr<float> U{ctx->u32};
+    const float k = (float)ctx->kappa;
+    if (mode == MODE_A) {
+      CloverPtrF32 c{ctx->cinv32};
+      dslash_kernel<float, MODE_A><<<grid, block, 0, st>>>(g, o, i, U, c, k);
+    } else {
+      CloverPtrF32 c{ctx->clov32};
+      if (mode == MODE_D) dslash_kernel<float, MODE_D><<<grid, block, 0, st>>>(g, o, i, U, c, k);
+      else dslash_kernel<float, MODE_DDAG><<<grid, block, 0, st>>>(g, o, i, U, c, k);
+    }
+    check_launch();
+  } else {
+    throw Error{QCD_ERR_ARG, "operator precision must be DOUBLE or SINGLE"};
+  }
+}
+
+void clover_apply_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int inverse, int nrhs,
+                         cudaStream_t st) {
+  const Geom& g = ctx->geom;
+  dim3 grid(grid_for(g.vol, 128), nrhs);
+  if (prec == QCD_PREC_DOUBLE) {
+    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+    F64Spinor o{(double2*)out}, i{(double2*)in};
+    CloverPtrF64 c{inverse ? ctx->cinv64 : ctx->clov64};
+    clover_apply_kernel<double><<<grid, 128, 0, st>>>(g, o, i, c);
+  } else if (prec == QCD_PREC_SINGLE) {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    F32Spinor o{(float4*)out}, i{(float4*)in};
+    CloverPtrF32 c{inverse ? ctx->cinv32 : ctx->clov32};
+    clover_apply_kernel<float><<<grid, 128, 0, st>>>(g, o, i, c);
+  } else {
+    throw Error{QCD_ERR_ARG, "clover precision must be DOUBLE or SINGLE"};
+  }
+  check_launch();
+}
+
+void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col, cudaStream_t st) {
+  const Geom& g = ctx->geom;
+  LaunchScope ls(ctx, QCD_KC_DSLASH, st);
+  ablock_kernel<<<grid_for(g.vol, 128), 128, 0, st>>>(g, F32Spinor{out}, F32Spinor{(float4*)in},
+                                                      LinkPtr<float>{ctx->u32}, CloverPtrF32{ctx->cinv32},
+                                                      (float)ctx->kappa, row, col);
+  check_launch();
+}
+
+}  // namespace qcd
+
+using namespace qcd;
+
+#define API_BEGIN try {
+#define API_END(ctx)                          \
+  }                                           \
+  catch (const qcd::Error& e) {               \
+    (ctx)->err = e.msg;                       \
+    return e.code;                            \
+  }                                           \
+  catch (...) {                               \
+    (ctx)->err = "unknown error";             \
+    return QCD_ERR_CUDA;                      \
+  }                                           \
+  return QCD_OK;
+
+static void require_operator(qcd_ctx* ctx) {
+  QCD_REQUIRE(ctx->have_gauge, QCD_ERR_STATE, "no gauge field set");
+  QCD_REQUIRE(ctx->have_clover, QCD_ERR_STATE, "clover term not built (qcd_build_clover)");
+}
+
+extern "C" int qcd_apply_D(qcd_ctx* ctx, void* out, const void* in, int prec, int dagger, int nrhs, void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  require_operator(ctx);
+  QCD_REQUIRE(out && in && out != in && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_apply_D: bad arguments");
+  dslash_launch(ctx, out, in, prec, dagger ? MODE_DDAG : MODE_D, nrhs, (cudaStream_t)stream);
+  API_END(ctx)
+}
+
+extern "C" int qcd_apply_A(qcd_ctx* ctx, void* out, const void* in, int nrhs, void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  require_operator(ctx);
+  QCD_REQUIRE(out && in && out != in && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_apply_A: bad arguments");
+  dslash_launch(ctx, out, in, QCD_PREC_SINGLE, MODE_A, nrhs, (cudaStream_t)stream);
+  API_END(ctx)
+}
+
+extern "C" int qcd_apply_clover(qcd_ctx* ctx, void* out, const void* in, int prec, int inverse, int nrhs,
+                                void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  require_operator(ctx);
+  QCD_REQUIRE(out && in && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_apply_clover: bad arguments");
+  clover_apply_launch(ctx, out, in, prec, inverse, nrhs, (cudaStream_t)stream);
+  API_END(ctx)
+}
+
+extern "C" int qcd_apply_A_block(qcd_ctx* ctx, void* out, const void* in, int row, int col, void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  require_operator(ctx);
+  QCD_REQUIRE(out && in && out != in && (row == 0 || row == 1) && (col == 0 || col == 1), QCD_ERR_ARG,
+              "qcd_apply_A_block: bad arguments");
+  ablock_launch(ctx, (float4*)out, (const float4*)in, row, col, (cudaStream_t)stream);
+  API_END(ctx)
+}

@@ -1,0 +1,588 @@
+// Internal types shared by the CUDA translation units of libqcd_gb300.
+//
+// Device layout ("internal layout"): the lattice is cut into domains of
+// d = (dx, dy, dz, dt) sites (powers of two, at most 256 sites).  Domains are
+// coloured by the parity of the sum of their domain coordinates (Sec. 3,
+// red/black domain decomposition); all even (E) domains come first, then all
+// odd (O) ones, each half in lexicographic domain order.  Inside a domain the
+// site index is s = ((t dz + z) dy + y) dx + x.  Every field is a structure of
+// arrays per domain so that a warp touching consecutive sites of a domain
+// issues one coalesced 128-bit (or 64-bit) access per component group:
+//
+//   quark float32 : float4  [rhs][domain][6 groups][vd]   (24 floats / site)
+//   quark float64 : double2 [rhs][domain][12 comps][vd]   (12 complex / site)
+//   quark float16 : uint4   [rhs][domain][3 groups][vd]   (24 halves / site)
+//                 + float   [rhs][domain][vd]            (per-site norm)
+//   links  float32: float2  [domain][mu][9][vd]           (3x3 complex)
+//   links  float64: double2 [domain][mu][9][vd]
+//   links  float16: __half2 [domain][mu][9][vd]
+//   clover float32: float4  [domain][18][vd]  (two packed 6x6 Hermitian blocks)
+//   clover float64: double2 [domain][36][vd]
+//   clover float16: __half2 [domain][36][vd]
+//
+// Quark components inside a site are ordered (spin, colour, re/im) in the
+// chiral gamma basis; the upper chirality (spins 0, 1) occupies float4
+// groups 0-2, the lower (spins 2, 3) groups 3-5, matching the two clover
+// blocks.  A packed Hermitian 6x6 block holds its 6 real diagonal entries
+// followed by the 15 complex entries (i < j) in row-major order; its index i
+// is (spin within the block) * 3 + colour.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "qcd_gb300.h"
+
+namespace qcd {
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+struct Geom {
+  int L[4];        // lattice extents x, y, z, t
+  int d[4];        // domain extents
+  int nd[4];       // domains per direction
+  int logd[4];     // log2 d_mu
+  int shift[4];    // bit offset of local coordinate mu inside s
+  int vd;          // sites per domain
+  int logvd;
+  int ndom;        // domains in total
+  int nhalf;       // domains per colour
+  long long vol;   // sites
+  int bc_t;        // +1 periodic, -1 antiperiodic in t
+  const int* nbr;  // [ndom][8]: neighbour domain across face 2 mu (+) / 2 mu + 1 (-)
+  const unsigned char* tflag;  // [ndom]: bit k set when face k crosses t = Lt-1 <-> 0
+};
+
+// Neighbouring site of (dom, s) in direction mu, forward (fwd) or backward.
+// Returns the sign of the boundary condition carried by the hop.
+__device__ __forceinline__ int nbr_site(const Geom& g, int dom, int s, int mu, bool fwd,
+                                        int& ndom_out, int& ns_out) {
+  const int c = (s >> g.shift[mu]) & (g.d[mu] - 1);
+  const int step = 1 << g.shift[mu];
+  if (fwd) {
+    if (c < g.d[mu] - 1) {
+      ndom_out = dom;
+      ns_out = s + step;
+      return 1;
+    }
+    ndom_out = __ldg(g.nbr + dom * 8 + 2 * mu);
+    ns_out = s - (g.d[mu] - 1) * step;
+    return ((__ldg(g.tflag + dom) >> (2 * mu)) & 1) ? g.bc_t : 1;
+  }
+  if (c > 0) {
+    ndom_out = dom;
+    ns_out = s - step;
+    return 1;
+  }
+  ndom_out = __ldg(g.nbr + dom * 8 + 2 * mu + 1);
+  ns_out = s + (g.d[mu] - 1) * step;
+  return ((__ldg(g.tflag + dom) >> (2 * mu + 1)) & 1) ? g.bc_t : 1;
+}
+
+// true when the hop (dom, s) -> direction mu stays inside the domain
+__device__ __forceinline__ bool hop_is_intra(const Geom& g, int s, int mu, bool fwd) {
+  const int c = (s >> g.shift[mu]) & (g.d[mu] - 1);
+  return fwd ? (c < g.d[mu] - 1) : (c > 0);
+}
+
+// Global coordinates -> (domain, local site).
+__device__ __forceinline__ void coords_to_internal(const Geom& g, const int x[4], int& dom, int& s) {
+  int dc[4];
+  s = 0;
+  int lex = 0;
+#pragma unroll
+  for (int mu = 3; mu >= 0; --mu) {
+    dc[mu] = x[mu] >> g.logd[mu];
+    lex = lex * g.nd[mu] + dc[mu];
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) s |= (x[mu] & (g.d[mu] - 1)) << g.shift[mu];
+  const int colour = (dc[0] + dc[1] + dc[2] + dc[3]) & 1;
+  dom = colour * g.nhalf + (lex >> 1);
+}
+
+// canonical site index n = ((t Lz + z) Ly + y) Lx + x -> coordinates
+__device__ __forceinline__ void site_coords(const Geom& g, long long n, int x[4]) {
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    x[mu] = (int)(n % g.L[mu]);
+    n /= g.L[mu];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// complex arithmetic
+// ---------------------------------------------------------------------------
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> make_cx(R a, R b) {
+  cx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return make_cx(a.re + b.re, a.im + b.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return make_cx(a.re - b.re, a.im - b.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return make_cx(-a.re, -a.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return make_cx(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R a, cx<R> b) { return make_cx(a * b.re, a * b.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> conjg(cx<R> a) { return make_cx(a.re, -a.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> times_i(cx<R> a) { return make_cx(-a.im, a.re); }
+template <typename R>
+__device__ __forceinline__ cx<R> times_mi(cx<R> a) { return make_cx(a.im, -a.re); }
+// acc + a * b
+template <typename R>
+__device__ __forceinline__ cx<R> cmac(cx<R> acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a) * b
+template <typename R>
+__device__ __forceinline__ cx<R> cmacc(cx<R> acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+
+template <typename R>
+struct Spinor {
+  cx<R> v[4][3];  // [spin][colour], chiral basis
+};
+template <typename R>
+struct HalfSpinor {
+  cx<R> h[2][3];
+};
+template <typename R>
+struct SU3 {
+  cx<R> m[3][3];
+};
+
+template <typename R>
+__device__ __forceinline__ void zero(Spinor<R>& a) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.v[s][c] = make_cx<R>(0, 0);
+}
+
+// ---------------------------------------------------------------------------
+// spin projection in the chiral basis
+//   gamma_4 = [[0, 1], [1, 0]],  gamma_k = [[0, -i sigma_k], [i sigma_k, 0]].
+// PM = -1 selects (1 - gamma_mu), PM = +1 selects (1 + gamma_mu).  project()
+// returns the two independent spin rows h (the upper half of the projected
+// spinor); accumulate() adds the full projected spinor rebuilt from U h.
+// ---------------------------------------------------------------------------
+template <int MU, int PM, typename R>
+__device__ __forceinline__ void project(const Spinor<R>& p, HalfSpinor<R>& h) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> u0 = p.v[0][c], u1 = p.v[1][c], l0 = p.v[2][c], l1 = p.v[3][c];
+    if (MU == 0) {
+      if (PM < 0) { h.h[0][c] = u0 + times_i(l1); h.h[1][c] = u1 + times_i(l0); }
+      else        { h.h[0][c] = u0 - times_i(l1); h.h[1][c] = u1 - times_i(l0); }
+    } else if (MU == 1) {
+      if (PM < 0) { h.h[0][c] = u0 + l1; h.h[1][c] = u1 - l0; }
+      else        { h.h[0][c] = u0 - l1; h.h[1][c] = u1 + l0; }
+    } else if (MU == 2) {
+      if (PM < 0) { h.h[0][c] = u0 + times_i(l0); h.h[1][c] = u1 - times_i(l1); }
+      else        { h.h[0][c] = u0 - times_i(l0); h.h[1][c] = u1 + times_i(l1); }
+    } else {
+      if (PM < 0) { h.h[0][c] = u0 - l0; h.h[1][c] = u1 - l1; }
+      else        { h.h[0][c] = u0 + l0; h.h[1][c] = u1 + l1; }
+    }
+  }
+}
+
+template <int MU, int PM, typename R>
+__device__ __forceinline__ void accumulate(Spinor<R>& acc, const HalfSpinor<R>& h) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> h0 = h.h[0][c], h1 = h.h[1][c];
+    acc.v[0][c] = acc.v[0][c] + h0;
+    acc.v[1][c] = acc.v[1][c] + h1;
+    if (MU == 0) {
+      if (PM < 0) { acc.v[2][c] = acc.v[2][c] + times_mi(h1); acc.v[3][c] = acc.v[3][c] + times_mi(h0); }
+      else        { acc.v[2][c] = acc.v[2][c] + times_i(h1);  acc.v[3][c] = acc.v[3][c] + times_i(h0); }
+    } else if (MU == 1) {
+      if (PM < 0) { acc.v[2][c] = acc.v[2][c] - h1; acc.v[3][c] = acc.v[3][c] + h0; }
+      else        { acc.v[2][c] = acc.v[2][c] + h1; acc.v[3][c] = acc.v[3][c] - h0; }
+    } else if (MU == 2) {
+      if (PM < 0) { acc.v[2][c] = acc.v[2][c] + times_mi(h0); acc.v[3][c] = acc.v[3][c] + times_i(h1); }
+      else        { acc.v[2][c] = acc.v[2][c] + times_i(h0);  acc.v[3][c] = acc.v[3][c] + times_mi(h1); }
+    } else {
+      if (PM < 0) { acc.v[2][c] = acc.v[2][c] - h0; acc.v[3][c] = acc.v[3][c] - h1; }
+      else        { acc.v[2][c] = acc.v[2][c] + h0; acc.v[3][c] = acc.v[3][c] + h1; }
+    }
+  }
+}
+
+// y = U h (both spin rows) or y = U^dag h
+template <typename R>
+__device__ __forceinline__ void su3_mul(const SU3<R>& u, const HalfSpinor<R>& h, HalfSpinor<R>& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cx<R> acc = u.m[a][0] * h.h[s][0];
+      acc = cmac(acc, u.m[a][1], h.h[s][1]);
+      acc = cmac(acc, u.m[a][2], h.h[s][2]);
+      y.h[s][a] = acc;
+    }
+}
+template <typename R>
+__device__ __forceinline__ void su3_dag_mul(const SU3<R>& u, const HalfSpinor<R>& h, HalfSpinor<R>& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cx<R> acc = make_cx<R>(0, 0);
+      acc = cmacc(acc, u.m[0][a], h.h[s][0]);
+      acc = cmacc(acc, u.m[1][a], h.h[s][1]);
+      acc = cmacc(acc, u.m[2][a], h.h[s][2]);
+      y.h[s][a] = acc;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void scale_half(HalfSpinor<R>& h, R f) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h.h[s][c] = f * h.h[s][c];
+}
+
+// offset of packed Hermitian entry (i, j), i < j, in a 6x6 block
+__host__ __device__ __forceinline__ int herm_off(int i, int j) { return 5 * i - (i * (i - 1)) / 2 + (j - i - 1); }
+
+// y = M x for one packed Hermitian 6x6 block given as 36 reals
+template <typename R, typename Load>
+__device__ __forceinline__ void herm6_mul(Load blk, const cx<R> x[6], cx<R> y[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y[i] = blk.diag(i) * x[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      const cx<R> a = blk.off(herm_off(i, j));
+      y[i] = cmac(y[i], a, x[j]);
+      y[j] = cmacc(y[j], a, x[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// field accessors
+// ---------------------------------------------------------------------------
+struct F32Spinor {
+  float4* p;
+  __device__ __forceinline__ size_t idx(const Geom& g, int dom, int grp, int s) const {
+    return ((size_t)(dom * 6 + grp) << g.logvd) + s;
+  }
+  __device__ __forceinline__ void load(const Geom& g, int dom, int s, Spinor<float>& a) const {
+    float f[24];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float4 v = __ldg(p + idx(g, dom, k, s));
+      f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.v[sp][c] = make_cx(f[(sp * 3 + c) * 2], f[(sp * 3 + c) * 2 + 1]);
+  }
+  __device__ __forceinline__ void store(const Geom& g, int dom, int s, const Spinor<float>& a) const {
+    float f[24];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { f[(sp * 3 + c) * 2] = a.v[sp][c].re; f[(sp * 3 + c) * 2 + 1] = a.v[sp][c].im; }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[idx(g, dom, k, s)] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+  }
+};
+
+struct F64Spinor {
+  double2* p;
+  __device__ __forceinline__ size_t idx(const Geom& g, int dom, int comp, int s) const {
+    return ((size_t)(dom * 12 + comp) << g.logvd) + s;
+  }
+  __device__ __forceinline__ void load(const Geom& g, int dom, int s, Spinor<double>& a) const {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double2 v = __ldg(p + idx(g, dom, sp * 3 + c, s));
+        a.v[sp][c] = make_cx(v.x, v.y);
+      }
+  }
+  __device__ __forceinline__ void store(const Geom& g, int dom, int s, const Spinor<double>& a) const {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) p[idx(g, dom, sp * 3 + c, s)] = make_double2(a.v[sp][c].re, a.v[sp][c].im);
+  }
+};
+
+// float16 storage: 24 halves scaled by a per-site float32 norm (max |component|)
+struct F16Spinor {
+  uint4* p;
+  float* nrm;
+  __device__ __forceinline__ size_t idx(const Geom& g, int dom, int grp, int s) const {
+    return ((size_t)(dom * 3 + grp) << g.logvd) + s;
+  }
+  __device__ __forceinline__ void load(const Geom& g, int dom, int s, Spinor<float>& a) const {
+    const float n = __ldg(nrm + ((size_t)dom << g.logvd) + s);
+    float f[24];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint4 v = __ldg(p + idx(g, dom, k, s));
+      const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __half2 h2 = *reinterpret_cast<const __half2*>(&w[j]);
+        const float2 ff = __half22float2(h2);
+        f[8 * k + 2 * j] = ff.x * n;
+        f[8 * k + 2 * j + 1] = ff.y * n;
+      }
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.v[sp][c] = make_cx(f[(sp * 3 + c) * 2], f[(sp * 3 + c) * 2 + 1]);
+  }
+  __device__ __forceinline__ void store(const Geom& g, int dom, int s, const Spinor<float>& a) const {
+    float f[24];
+    float m = 0.f;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        f[(sp * 3 + c) * 2] = a.v[sp][c].re;
+        f[(sp * 3 + c) * 2 + 1] = a.v[sp][c].im;
+        m = fmaxf(m, fmaxf(fabsf(a.v[sp][c].re), fabsf(a.v[sp][c].im)));
+      }
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    nrm[((size_t)dom << g.logvd) + s] = m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      unsigned w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __half2 h2 = __floats2half2_rn(f[8 * k + 2 * j] * inv, f[8 * k + 2 * j + 1] * inv);
+        w[j] = *reinterpret_cast<unsigned*>(&h2);
+      }
+      p[idx(g, dom, k, s)] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+};
+
+template <typename R>
+struct LinkPtr;
+template <>
+struct LinkPtr<float> {
+  const float2* p;
+  __device__ __forceinline__ void load(const Geom& g, int dom, int mu, int s, SU3<float>& u) const {
+    const size_t base = ((size_t)((dom * 4 + mu) * 9)) << g.logvd;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float2 v = __ldg(p + base + ((size_t)e << g.logvd) + s);
+      u.m[e / 3][e % 3] = make_cx(v.x, v.y);
+    }
+  }
+};
+template <>
+struct LinkPtr<double> {
+  const double2* p;
+  __device__ __forceinline__ void load(const Geom& g, int dom, int mu, int s, SU3<double>& u) const {
+    const size_t base = ((size_t)((dom * 4 + mu) * 9)) << g.logvd;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const double2 v = __ldg(p + base + ((size_t)e << g.logvd) + s);
+      u.m[e / 3][e % 3] = make_cx(v.x, v.y);
+    }
+  }
+};
+struct LinkPtrHalf {
+  const __half2* p;
+  __device__ __forceinline__ void load(const Geom& g, int dom, int mu, int s, SU3<float>& u) const {
+    const size_t base = ((size_t)((dom * 4 + mu) * 9)) << g.logvd;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float2 v = __half22float2(__ldg(p + base + ((size_t)e << g.logvd) + s));
+      u.m[e / 3][e % 3] = make_cx(v.x, v.y);
+    }
+  }
+};
+
+// packed clover block readers (block b = 0 upper, 1 lower)
+struct CloverBlockF32 {
+  float r[36];
+  __device__ __forceinline__ float diagv(int i) const { return r[i]; }
+  __device__ __forceinline__ cx<float> diag(int i) const { return make_cx(r[i], 0.f); }
+  __device__ __forceinline__ cx<float> off(int k) const { return make_cx(r[6 + 2 * k], r[7 + 2 * k]); }
+};
+struct CloverBlockF64 {
+  double r[36];
+  __device__ __forceinline__ cx<double> diag(int i) const { return make_cx(r[i], 0.0); }
+  __device__ __forceinline__ cx<double> off(int k) const { return make_cx(r[6 + 2 * k], r[7 + 2 * k]); }
+};
+
+struct CloverPtrF32 {
+  const float4* p;
+  __device__ __forceinline__ void load_block(const Geom& g, int dom, int s, int b, CloverBlockF32& blk) const {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = __ldg(p + (((size_t)(dom * 18 + 9 * b + k)) << g.logvd) + s);
+      blk.r[4 * k] = v.x; blk.r[4 * k + 1] = v.y; blk.r[4 * k + 2] = v.z; blk.r[4 * k + 3] = v.w;
+    }
+  }
+};
+struct CloverPtrF64 {
+  const double2* p;
+  __device__ __forceinline__ void load_block(const Geom& g, int dom, int s, int b, CloverBlockF64& blk) const {
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      const double2 v = __ldg(p + (((size_t)(dom * 36 + 18 * b + k)) << g.logvd) + s);
+      blk.r[2 * k] = v.x; blk.r[2 * k + 1] = v.y;
+    }
+  }
+};
+struct CloverPtrF16 {
+  const __half2* p;
+  __device__ __forceinline__ void load_block(const Geom& g, int dom, int s, int b, CloverBlockF32& blk) const {
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      const float2 v = __half22float2(__ldg(p + (((size_t)(dom * 36 + 18 * b + k)) << g.logvd) + s));
+      blk.r[2 * k] = v.x; blk.r[2 * k + 1] = v.y;
+    }
+  }
+};
+
+// psi <- M psi with the two chiral blocks of a clover field
+template <typename R, typename Ptr, typename Blk>
+__device__ __forceinline__ void clover_mul(const Ptr& cp, const Geom& g, int dom, int s, Spinor<R>& psi) {
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    Blk blk;
+    cp.load_block(g, dom, s, b, blk);
+    cx<R> x[6], y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = psi.v[2 * b + i / 3][i % 3];
+    herm6_mul<R>(blk, x, y);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) psi.v[2 * b + i / 3][i % 3] = y[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// context (host side)
+// ---------------------------------------------------------------------------
+struct Workspace;
+struct Profiler;
+
+}  // namespace qcd
+
+struct qcd_ctx {
+  qcd::Geom geom;
+  int basis = QCD_BASIS_CHIRAL;
+  int device = 0;
+  double kappa = 0.125, csw = 1.0;
+  bool have_gauge = false, have_clover = false;
+  // device arrays owned by the context
+  int* d_nbr = nullptr;
+  unsigned char* d_tflag = nullptr;
+  double2* u64 = nullptr;
+  float2* u32 = nullptr;
+  __half2* u16 = nullptr;
+  double2* clov64 = nullptr;     // 1 + C
+  float4* clov32 = nullptr;
+  double2* cinv64 = nullptr;     // (1 + C)^-1
+  float4* cinv32 = nullptr;
+  __half2* cinv16 = nullptr;
+  int* d_status = nullptr;       // device status word (non-finite, ...)
+  qcd::Workspace* ws = nullptr;
+  qcd::Profiler* prof = nullptr;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace qcd {
+
+// error helpers used by the C entry points
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define QCD_CUDA_CHECK(call)                                                            \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw ::qcd::Error{e_ == cudaErrorMemoryAllocation ? QCD_ERR_OOM : QCD_ERR_CUDA,   \
+                         std::string(#call) + ": " + cudaGetErrorString(e_)};            \
+  } while (0)
+
+#define QCD_REQUIRE(cond, code, msg)                  \
+  do {                                                \
+    if (!(cond)) throw ::qcd::Error{(code), (msg)};   \
+  } while (0)
+
+// launch bookkeeping: profiling events and the launch counter
+void launch_begin(qcd_ctx* ctx, int kclass, cudaStream_t st);
+void launch_end(qcd_ctx* ctx, int kclass, cudaStream_t st);
+
+struct LaunchScope {
+  qcd_ctx* ctx;
+  int kc;
+  cudaStream_t st;
+  LaunchScope(qcd_ctx* c, int k, cudaStream_t s) : ctx(c), kc(k), st(s) { launch_begin(c, k, s); }
+  ~LaunchScope() { launch_end(ctx, kc, st); }
+};
+
+inline void check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error{QCD_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+inline size_t spinor_bytes(const Geom& g, int prec) {
+  const size_t v = (size_t)g.vol;
+  if (prec == QCD_PREC_DOUBLE) return v * 24 * sizeof(double);
+  if (prec == QCD_PREC_SINGLE) return v * 24 * sizeof(float);
+  return v * (24 * sizeof(__half) + sizeof(float));
+}
+
+inline int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+// internal entry points implemented in the other translation units
+void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st);
+void clover_apply_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int inverse, int nrhs,
+                         cudaStream_t st);
+void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col, cudaStream_t st);
+void build_clover_launch(qcd_ctx* ctx, cudaStream_t st);
+void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
+
+// dslash modes
+enum { MODE_D = 0, MODE_DDAG = 1, MODE_A = 2 };
+
+}  // namespace qcd

@@ -1,0 +1,787 @@
+// BiCGStab (Algorithm 5) on A M_SAP, the float64 defect-correction loop
+// (Algorithm 4) and the fused BLAS-1 kernels they use (arXiv:2109.10687,
+// Sec. 3).
+//
+// Reductions: every reducing kernel accumulates per thread in float32,
+// combines warps and blocks in float64 and lets the last block to finish sum
+// the per-block partials in a fixed order, so results do not depend on
+// scheduling.  The scalars of the iteration (rho_0, alpha, omega, beta,
+// |r|^2) live in device memory, one record per right-hand side, and are
+// computed by the last block of the reduction that produces them; the host
+// only reads the per-rhs "done" flags to decide when to leave the loop.
+//
+// Solution accumulation: Algorithm 5 iterates y and finishes with
+// x = M_SAP y.  Here every A M_SAP p also yields z = M_SAP p, and the solution
+// is accumulated as x += alpha z_p + omega z_r, which equals M_SAP y by the
+// linearity of M_SAP and keeps the recursive residual tied to the true one
+// when the preconditioner runs in reduced precision.
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int n_sap, int n_jac, int sap_prec, void* ws_s,
+                      void* ws_x16, void* ws_b16, cudaStream_t st);
+
+struct Scal {
+  double rho0_re, rho0_im;
+  double alpha_re, alpha_im;
+  double omega_re, omega_im;
+  double beta_re, beta_im;
+  double rnorm2, bnorm2;
+  double tol2;  // stop when rnorm2 < tol2 * bnorm2
+  double aux;
+  int done;     // 1: converged or failed; no further updates
+  int status;   // QCD_OK, QCD_ERR_BREAKDOWN, QCD_ERR_NONFINITE
+  int conv;     // 1: converged
+  int pad;
+};
+
+struct Workspace {
+  int nrhs = 0;
+  size_t v4 = 0;  // float4 per rhs
+  float4 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *t = nullptr, *zp = nullptr, *zr = nullptr,
+         *rt = nullptr, *tmp32 = nullptr;
+  void *sap_s = nullptr, *sap_x16 = nullptr, *sap_b16 = nullptr;
+  double2 *x64 = nullptr, *r64 = nullptr, *b64 = nullptr, *t64 = nullptr;
+  double* partials = nullptr;
+  double* dres = nullptr;   // small device results: 4 doubles per rhs
+  unsigned* counters = nullptr;
+  Scal* scal = nullptr;
+  Scal* h_scal = nullptr;  // pinned
+  double* h_red = nullptr; // pinned
+  int nblocks = 0;
+};
+
+void workspace_free(qcd_ctx* ctx) {
+  Workspace* w = ctx->ws;
+  if (!w) return;
+  void* ptrs[] = {w->x, w->r, w->p, w->q, w->t, w->zp, w->zr, w->rt, w->tmp32, w->sap_s, w->sap_x16, w->sap_b16,
+                  w->x64, w->r64, w->b64, w->t64, w->partials, w->dres, w->counters, w->scal};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (w->h_scal) cudaFreeHost(w->h_scal);
+  if (w->h_red) cudaFreeHost(w->h_red);
+  delete w;
+  ctx->ws = nullptr;
+}
+
+static constexpr int RED_THREADS = 256;
+static constexpr int MAX_RED_OUT = 4;
+
+// Allocate (or grow) the workspace for nrhs right-hand sides.  The reduction
+// buffers are always present; the solver vectors only with `solver`.
+static Workspace* workspace(qcd_ctx* ctx, int nrhs, bool solver) {
+  Workspace* w = ctx->ws;
+  const bool have_solver = w && w->x;
+  if (w && w->nrhs >= nrhs && (have_solver || !solver)) return w;
+  const int keep_nrhs = w ? std::max(w->nrhs, nrhs) : nrhs;
+  const bool want_solver = solver || have_solver;
+  workspace_free(ctx);
+  w = new Workspace();
+  ctx->ws = w;
+  const Geom& g = ctx->geom;
+  w->nrhs = keep_nrhs;
+  w->v4 = (size_t)g.vol * 6;
+  int dev = 0, sms = 0;
+  QCD_CUDA_CHECK(cudaGetDevice(&dev));
+  QCD_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  w->nblocks = std::max(1, std::min(4 * sms, (int)((w->v4 + RED_THREADS - 1) / RED_THREADS)));
+  QCD_CUDA_CHECK(cudaMalloc(&w->partials, sizeof(double) * MAX_RED_OUT * w->nblocks * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMalloc(&w->dres, sizeof(double) * 4 * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMalloc(&w->counters, sizeof(unsigned) * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMemset(w->counters, 0, sizeof(unsigned) * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMalloc(&w->scal, sizeof(Scal) * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMemset(w->scal, 0, sizeof(Scal) * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMallocHost(&w->h_scal, sizeof(Scal) * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMallocHost(&w->h_red, sizeof(double) * MAX_RED_OUT * keep_nrhs));
+  if (want_solver) {
+    const size_t b32 = w->v4 * sizeof(float4) * keep_nrhs;
+    float4** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->t, &w->zp, &w->zr, &w->rt, &w->tmp32};
+    for (auto v : vecs) QCD_CUDA_CHECK(cudaMalloc(v, b32));
+    const size_t b64 = (size_t)g.vol * 12 * sizeof(double2) * keep_nrhs;
+    double2** v64[] = {&w->x64, &w->r64, &w->b64, &w->t64};
+    for (auto v : v64) QCD_CUDA_CHECK(cudaMalloc(v, b64));
+    QCD_CUDA_CHECK(cudaMalloc(&w->sap_s, spinor_bytes(g, QCD_PREC_SINGLE)));
+    QCD_CUDA_CHECK(cudaMalloc(&w->sap_x16, spinor_bytes(g, QCD_PREC_HALF)));
+    QCD_CUDA_CHECK(cudaMalloc(&w->sap_b16, spinor_bytes(g, QCD_PREC_HALF)));
+  }
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// reduction machinery
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void block_sum(double v[N], double* sh /* [32][N] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) sh[warp * N + k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      v[k] = lane < nw ? sh[lane * N + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+  }
+  __syncthreads();
+}
+
+// Writes this block's partials; returns true (in every thread) in the block
+// that finished last, which then holds the totals in tot[] (all threads).
+template <int N>
+__device__ bool grid_reduce(double v[N], double* partials, unsigned* counter, double tot[N]) {
+  __shared__ double sh[32 * N];
+  __shared__ bool is_last;
+  block_sum<N>(v, sh);
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) partials[blockIdx.x * N + k] = v[k];
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    is_last = prev == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double w[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) w[k] = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] += __ldcg(partials + i * N + k);
+  block_sum<N>(w, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) sh[k] = w[k];
+    *counter = 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) tot[k] = sh[k];
+  __syncthreads();
+  return true;
+}
+
+// complex (a.x + i a.y) * (b.x + i b.y) for the two complex numbers of a float4
+__device__ __forceinline__ float4 caxpy4(float ar, float ai, float4 xv, float4 y) {
+  y.x = fmaf(ar, xv.x, fmaf(-ai, xv.y, y.x));
+  y.y = fmaf(ar, xv.y, fmaf(ai, xv.x, y.y));
+  y.z = fmaf(ar, xv.z, fmaf(-ai, xv.w, y.z));
+  y.w = fmaf(ar, xv.w, fmaf(ai, xv.z, y.w));
+  return y;
+}
+__device__ __forceinline__ void cdot_acc(float4 a, float4 b, float& re, float& im) {
+  re = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, re))));
+  im = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, im))));
+}
+__device__ __forceinline__ float norm4(float4 a) { return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w; }
+
+#define RHS_SETUP                                                     \
+  const int rhs = blockIdx.y;                                         \
+  Scal& sc = scal[rhs];                                               \
+  const size_t off = (size_t)rhs * n4;                                \
+  double* part = partials + (size_t)rhs * MAX_RED_OUT * gridDim.x;    \
+  unsigned* cnt = counters + rhs;
+
+// |a|^2 -> out[rhs]
+__global__ void k_norm2(const float4* __restrict__ a, size_t n4, double* out, double* partials, unsigned* counters,
+                        Scal* scal) {
+  RHS_SETUP
+  (void)sc;
+  float s = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    s += norm4(a[off + i]);
+  double v[1] = {s}, tot[1];
+  if (grid_reduce<1>(v, part, cnt, tot) && threadIdx.x == 0) out[rhs] = tot[0];
+}
+
+// <a|b> -> out[2 rhs], out[2 rhs + 1]
+__global__ void k_cdot(const float4* __restrict__ a, const float4* __restrict__ b, size_t n4, double* out,
+                       double* partials, unsigned* counters, Scal* scal) {
+  RHS_SETUP
+  (void)sc;
+  float re = 0.f, im = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    cdot_acc(a[off + i], b[off + i], re, im);
+  double v[2] = {re, im}, tot[2];
+  if (grid_reduce<2>(v, part, cnt, tot) && threadIdx.x == 0) {
+    out[2 * rhs] = tot[0];
+    out[2 * rhs + 1] = tot[1];
+  }
+}
+
+// BiCGStab initialisation: x = 0, r = p = rt = b, bnorm2 = |b|^2, rho_0 = bnorm2
+__global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float4* p, float4* rt, size_t n4,
+                       double tol2, Scal* scal, double* partials, unsigned* counters) {
+  RHS_SETUP
+  float s = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = b[off + i];
+    x[off + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r[off + i] = v;
+    p[off + i] = v;
+    rt[off + i] = v;
+    s += norm4(v);
+  }
+  double v[1] = {s}, tot[1];
+  if (grid_reduce<1>(v, part, cnt, tot) && threadIdx.x == 0) {
+    sc.bnorm2 = tot[0];
+    sc.rnorm2 = tot[0];
+    sc.rho0_re = tot[0];
+    sc.rho0_im = 0.0;
+    sc.tol2 = tol2;
+    sc.status = QCD_OK;
+    sc.conv = tot[0] == 0.0;
+    sc.done = tot[0] == 0.0;
+    if (!isfinite(tot[0])) {
+      sc.status = QCD_ERR_NONFINITE;
+      sc.done = 1;
+    }
+  }
+}
+
+// alpha = rho_0 / <rt|q>
+__global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict__ q, size_t n4, Scal* scal,
+                        double* partials, unsigned* counters) {
+  RHS_SETUP
+  if (sc.done) return;
+  float re = 0.f, im = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    cdot_acc(rt[off + i], q[off + i], re, im);
+  double v[2] = {re, im}, tot[2];
+  if (grid_reduce<2>(v, part, cnt, tot) && threadIdx.x == 0) {
+    const double dn = tot[0] * tot[0] + tot[1] * tot[1];
+    if (!(dn > 0.0) || !isfinite(dn)) {
+      sc.status = isfinite(dn) ? QCD_ERR_BREAKDOWN : QCD_ERR_NONFINITE;
+      sc.done = 1;
+    } else {
+      sc.alpha_re = (sc.rho0_re * tot[0] + sc.rho0_im * tot[1]) / dn;
+      sc.alpha_im = (sc.rho0_im * tot[0] - sc.rho0_re * tot[1]) / dn;
+    }
+  }
+}
+
+// x += alpha z; r -= alpha q; rnorm2 = |r|^2; first exit test
+__global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ q, size_t n4,
+                          Scal* scal, double* partials, unsigned* counters) {
+  RHS_SETUP
+  if (sc.done) return;
+  const float ar = (float)sc.alpha_re, ai = (float)sc.alpha_im;
+  float s = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    x[off + i] = caxpy4(ar, ai, z[off + i], x[off + i]);
+    const float4 rv = caxpy4(-ar, -ai, q[off + i], r[off + i]);
+    r[off + i] = rv;
+    s += norm4(rv);
+  }
+  double v[1] = {s}, tot[1];
+  if (grid_reduce<1>(v, part, cnt, tot) && threadIdx.x == 0) {
+    sc.rnorm2 = tot[0];
+    if (!isfinite(tot[0])) {
+      sc.status = QCD_ERR_NONFINITE;
+      sc.done = 1;
+    } else if (tot[0] < sc.tol2 * sc.bnorm2) {
+      sc.conv = 1;
+      sc.done = 1;
+    }
+  }
+}
+
+// omega = <t|r> / |t|^2
+__global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__ r, size_t n4, Scal* scal,
+                        double* partials, unsigned* counters) {
+  RHS_SETUP
+  if (sc.done) return;
+  float re = 0.f, im = 0.f, tt = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 tv = t[off + i];
+    cdot_acc(tv, r[off + i], re, im);
+    tt += norm4(tv);
+  }
+  double v[3] = {re, im, tt}, tot[3];
+  if (grid_reduce<3>(v, part, cnt, tot) && threadIdx.x == 0) {
+    if (!(tot[2] > 0.0) || !isfinite(tot[2])) {
+      sc.status = isfinite(tot[2]) ? QCD_ERR_BREAKDOWN : QCD_ERR_NONFINITE;
+      sc.done = 1;
+    } else {
+      sc.omega_re = tot[0] / tot[2];
+      sc.omega_im = tot[1] / tot[2];
+    }
+  }
+}
+
+// x += omega z; r -= omega t; rnorm2 = |r|^2, rho = <rt|r>; second exit test;
+// beta = alpha rho / (rho_0 omega); rho_0 = rho
+__global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ t,
+                          const float4* __restrict__ rt, size_t n4, Scal* scal, double* partials, unsigned* counters) {
+  RHS_SETUP
+  if (sc.done) return;
+  const float wr = (float)sc.omega_re, wi = (float)sc.omega_im;
+  float s = 0.f, re = 0.f, im = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    x[off + i] = caxpy4(wr, wi, z[off + i], x[off + i]);
+    const float4 rv = caxpy4(-wr, -wi, t[off + i], r[off + i]);
+    r[off + i] = rv;
+    s += norm4(rv);
+    cdot_acc(rt[off + i], rv, re, im);
+  }
+  double v[3] = {s, re, im}, tot[3];
+  if (grid_reduce<3>(v, part, cnt, tot) && threadIdx.x == 0) {
+    sc.rnorm2 = tot[0];
+    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
+      sc.status = QCD_ERR_NONFINITE;
+      sc.done = 1;
+    } else if (tot[0] < sc.tol2 * sc.bnorm2) {
+      sc.conv = 1;
+      sc.done = 1;
+    } else {
+      // beta = (alpha rho) / (rho_0 omega)
+      const double nr = sc.alpha_re * tot[1] - sc.alpha_im * tot[2];
+      const double ni = sc.alpha_re * tot[2] + sc.alpha_im * tot[1];
+      const double dr = sc.rho0_re * sc.omega_re - sc.rho0_im * sc.omega_im;
+      const double di = sc.rho0_re * sc.omega_im + sc.rho0_im * sc.omega_re;
+      const double dn = dr * dr + di * di;
+      if (!(dn > 0.0) || (tot[1] == 0.0 && tot[2] == 0.0)) {
+        sc.status = QCD_ERR_BREAKDOWN;
+        sc.done = 1;
+      } else {
+        sc.beta_re = (nr * dr + ni * di) / dn;
+        sc.beta_im = (ni * dr - nr * di) / dn;
+        sc.rho0_re = tot[1];
+        sc.rho0_im = tot[2];
+      }
+    }
+  }
+}
+
+// p = r + beta (p - omega q)
+__global__ void k_update_p(float4* p, const float4* __restrict__ r, const float4* __restrict__ q, size_t n4,
+                           const Scal* scal) {
+  const int rhs = blockIdx.y;
+  const Scal& sc = scal[rhs];
+  if (sc.done) return;
+  const size_t off = (size_t)rhs * n4;
+  const float br = (float)sc.beta_re, bi = (float)sc.beta_im;
+  const float wr = (float)sc.omega_re, wi = (float)sc.omega_im;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 tmp = caxpy4(-wr, -wi, q[off + i], p[off + i]);
+    p[off + i] = caxpy4(br, bi, tmp, r[off + i]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// float64 helpers for Algorithm 4 (two doubles per complex, 12 complex/site)
+// ---------------------------------------------------------------------------
+// out[rhs] = |a|^2 (float64 accumulation throughout)
+__global__ void k_norm2_f64(const double2* __restrict__ a, size_t n2, double* out, double* partials,
+                            unsigned* counters) {
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n2;
+  double* part = partials + (size_t)rhs * MAX_RED_OUT * gridDim.x;
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = a[off + i];
+    s = fma(v.x, v.x, fma(v.y, v.y, s));
+  }
+  double v[1] = {s}, tot[1];
+  if (grid_reduce<1>(v, part, counters + rhs, tot) && threadIdx.x == 0) out[rhs] = tot[0];
+}
+
+// r = b - r (r holds D x on entry); out[rhs] = |r|^2
+__global__ void k_residual_f64(const double2* __restrict__ b, double2* r, size_t n2, double* out, double* partials,
+                               unsigned* counters) {
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n2;
+  double* part = partials + (size_t)rhs * MAX_RED_OUT * gridDim.x;
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 bv = b[off + i], dv = r[off + i];
+    const double2 v = make_double2(bv.x - dv.x, bv.y - dv.y);
+    r[off + i] = v;
+    s = fma(v.x, v.x, fma(v.y, v.y, s));
+  }
+  double v[1] = {s}, tot[1];
+  if (grid_reduce<1>(v, part, counters + rhs, tot) && threadIdx.x == 0) out[rhs] = tot[0];
+}
+
+// float32 p = R_SP(r / err): same internal site order, float64 complex ->
+// float32 pairs (the float64 and float32 layouts order components alike
+// within a domain: float4 group k holds complex components 2k, 2k+1)
+__global__ void k_f64_to_f32_scaled(Geom g, const double2* __restrict__ r, float4* p, const double* scale) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int rhs = blockIdx.y;
+  const int dom = (int)(gid >> g.logvd) + rhs * g.ndom, s = (int)(gid & (g.vd - 1));
+  const double f = scale[rhs];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double2 a = r[((size_t)(dom * 12 + 2 * k) << g.logvd) + s];
+    const double2 b = r[((size_t)(dom * 12 + 2 * k + 1) << g.logvd) + s];
+    p[((size_t)(dom * 6 + k) << g.logvd) + s] = make_float4((float)(a.x * f), (float)(a.y * f), (float)(b.x * f),
+                                                            (float)(b.y * f));
+  }
+}
+
+// x64 += err * P_DP(q32)
+__global__ void k_f64_axpy_f32(Geom g, double2* x, const float4* __restrict__ q, const double* scale) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int rhs = blockIdx.y;
+  const int dom = (int)(gid >> g.logvd) + rhs * g.ndom, s = (int)(gid & (g.vd - 1));
+  const double f = scale[rhs];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 v = q[((size_t)(dom * 6 + k) << g.logvd) + s];
+    double2& a = x[((size_t)(dom * 12 + 2 * k) << g.logvd) + s];
+    double2& b = x[((size_t)(dom * 12 + 2 * k + 1) << g.logvd) + s];
+    a.x = fma(f, (double)v.x, a.x);
+    a.y = fma(f, (double)v.y, a.y);
+    b.x = fma(f, (double)v.z, b.x);
+    b.y = fma(f, (double)v.w, b.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+struct Launcher {
+  qcd_ctx* ctx;
+  Workspace* w;
+  cudaStream_t st;
+  int nrhs;
+  dim3 grid() const { return dim3(w->nblocks, nrhs); }
+};
+
+static void am_sap(qcd_ctx* ctx, Workspace* w, float4* z, float4* out, const float4* in, int nrhs, int n_sap, int n_jac,
+                   int sap_prec, cudaStream_t st) {
+  for (int r = 0; r < nrhs; ++r)
+    sap_apply_launch(ctx, z + r * w->v4, in + r * w->v4, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16, w->sap_b16, st);
+  dslash_launch(ctx, out, z, QCD_PREC_SINGLE, MODE_A, nrhs, st);
+}
+
+static bool all_done(Workspace* w, int nrhs, cudaStream_t st) {
+  QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(Scal) * nrhs, cudaMemcpyDeviceToHost, st));
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrhs; ++r)
+    if (!w->h_scal[r].done) return false;
+  return true;
+}
+
+// One iteration of Algorithm 5 (both half-steps); usable for graph capture.
+static void bicg_half1(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_params& P, cudaStream_t st) {
+  const dim3 grid(w->nblocks, nrhs);
+  am_sap(ctx, w, w->zp, w->q, w->p, nrhs, P.n_sap, P.n_jac, P.sap_prec, st);
+  LaunchScope ls(ctx, QCD_KC_BLAS, st);
+  k_alpha<<<grid, RED_THREADS, 0, st>>>(w->rt, w->q, w->v4, w->scal, w->partials, w->counters);
+  k_update1<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zp, w->q, w->v4, w->scal, w->partials, w->counters);
+  ctx->launches++;
+  check_launch();
+}
+static void bicg_half2(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_params& P, cudaStream_t st) {
+  const dim3 grid(w->nblocks, nrhs);
+  am_sap(ctx, w, w->zr, w->t, w->r, nrhs, P.n_sap, P.n_jac, P.sap_prec, st);
+  LaunchScope ls(ctx, QCD_KC_BLAS, st);
+  k_omega<<<grid, RED_THREADS, 0, st>>>(w->t, w->r, w->v4, w->scal, w->partials, w->counters);
+  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zr, w->t, w->rt, w->v4, w->scal, w->partials, w->counters);
+  k_update_p<<<grid, RED_THREADS, 0, st>>>(w->p, w->r, w->q, w->v4, w->scal);
+  ctx->launches += 2;
+  check_launch();
+}
+
+// Algorithm 5 on A M_SAP z = b32 (float32 internal fields, nrhs stacked);
+// solution accumulated in w->x.  Returns iterations; fills per-rhs status.
+static int bicgstab_sap(qcd_ctx* ctx, Workspace* w, const float4* b32, int nrhs, const qcd_solve_params& P,
+                        cudaStream_t st, int* worst_status) {
+  const dim3 grid(w->nblocks, nrhs);
+  {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    k_init<<<grid, RED_THREADS, 0, st>>>(b32, w->x, w->r, w->p, w->rt, w->v4, P.inner_tol * P.inner_tol, w->scal,
+                                         w->partials, w->counters);
+    check_launch();
+  }
+  int it = 0;
+  cudaGraphExec_t g1 = nullptr, g2 = nullptr;
+  long long n1 = 0, n2 = 0;  // kernels per captured half-iteration
+  if (P.use_graph) {
+    // capture each half-iteration once and replay it; the launch counter
+    // advances by the kernels of a graph on every replay
+    cudaGraph_t gr;
+    long long c0 = ctx->launches;
+    QCD_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    bicg_half1(ctx, w, nrhs, P, st);
+    QCD_CUDA_CHECK(cudaStreamEndCapture(st, &gr));
+    QCD_CUDA_CHECK(cudaGraphInstantiate(&g1, gr, 0));
+    cudaGraphDestroy(gr);
+    n1 = ctx->launches - c0;
+    c0 = ctx->launches;
+    QCD_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    bicg_half2(ctx, w, nrhs, P, st);
+    QCD_CUDA_CHECK(cudaStreamEndCapture(st, &gr));
+    QCD_CUDA_CHECK(cudaGraphInstantiate(&g2, gr, 0));
+    cudaGraphDestroy(gr);
+    n2 = ctx->launches - c0;
+    ctx->launches -= n1 + n2;
+  }
+  bool finished = all_done(w, nrhs, st);
+  while (!finished && it < P.max_inner) {
+    ++it;
+    if (g1) {
+      QCD_CUDA_CHECK(cudaGraphLaunch(g1, st));
+      ctx->launches += n1;
+    } else {
+      bicg_half1(ctx, w, nrhs, P, st);
+    }
+    if (all_done(w, nrhs, st)) break;
+    if (g2) {
+      QCD_CUDA_CHECK(cudaGraphLaunch(g2, st));
+      ctx->launches += n2;
+    } else {
+      bicg_half2(ctx, w, nrhs, P, st);
+    }
+    finished = all_done(w, nrhs, st);
+  }
+  if (g1) cudaGraphExecDestroy(g1);
+  if (g2) cudaGraphExecDestroy(g2);
+  int worst = QCD_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    const Scal& s = w->h_scal[r];
+    if (s.status != QCD_OK) worst = s.status;
+    else if (!s.conv && worst == QCD_OK) worst = QCD_ERR_NOT_CONVERGED;
+  }
+  *worst_status = worst;
+  return it;
+}
+
+}  // namespace qcd
+
+using namespace qcd;
+
+#define API_BEGIN try {
+#define API_END(ctx)                          \
+  }                                           \
+  catch (const qcd::Error& e) {               \
+    (ctx)->err = e.msg;                       \
+    return e.code;                            \
+  }                                           \
+  catch (...) {                               \
+    (ctx)->err = "unknown error";             \
+    return QCD_ERR_CUDA;                      \
+  }                                           \
+  return QCD_OK;
+
+static void require_operator(qcd_ctx* ctx) {
+  QCD_REQUIRE(ctx->have_gauge, QCD_ERR_STATE, "no gauge field set");
+  QCD_REQUIRE(ctx->have_clover, QCD_ERR_STATE, "clover term not built (qcd_build_clover)");
+}
+
+extern "C" int qcd_solve_params_default(qcd_solve_params* p) {
+  if (!p) return QCD_ERR_ARG;
+  p->tol = 1e-10;
+  p->inner_tol = 1e-6;
+  p->max_outer = 20;
+  p->max_inner = 500;
+  p->n_sap = 4;
+  p->n_jac = 4;
+  p->sap_prec = QCD_PREC_SINGLE;
+  p->use_graph = 0;
+  p->x_is_guess = 0;
+  return QCD_OK;
+}
+
+extern "C" int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac, int sap_prec, int with_A,
+                             void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  require_operator(ctx);
+  QCD_REQUIRE(out && in && out != in, QCD_ERR_ARG, "qcd_sap_apply: bad buffers");
+  QCD_REQUIRE(n_sap >= 0 && n_jac >= 1, QCD_ERR_ARG, "qcd_sap_apply: n_sap >= 0 and n_jac >= 1");
+  QCD_REQUIRE(sap_prec == QCD_PREC_SINGLE || sap_prec == QCD_PREC_HALF, QCD_ERR_ARG,
+              "qcd_sap_apply: sap_prec must be SINGLE or HALF");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace* w = workspace(ctx, 1, true);
+  if (with_A) {
+    am_sap(ctx, w, w->tmp32, (float4*)out, (const float4*)in, 1, n_sap, n_jac, sap_prec, st);
+  } else {
+    sap_apply_launch(ctx, (float4*)out, (const float4*)in, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16, w->sap_b16,
+                     st);
+  }
+  API_END(ctx)
+}
+
+extern "C" int qcd_norm2(qcd_ctx* ctx, double* result, const void* a, int prec, int nrhs, void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  QCD_REQUIRE(result && a && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_norm2: bad arguments");
+  QCD_REQUIRE(prec == QCD_PREC_SINGLE || prec == QCD_PREC_DOUBLE, QCD_ERR_ARG, "qcd_norm2: SINGLE or DOUBLE");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace* w = workspace(ctx, nrhs, false);
+  double* res = w->dres;
+  {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    if (prec == QCD_PREC_SINGLE)
+      k_norm2<<<dim3(w->nblocks, nrhs), RED_THREADS, 0, st>>>((const float4*)a, w->v4, res, w->partials, w->counters,
+                                                             w->scal);
+    else
+      k_norm2_f64<<<dim3(w->nblocks, nrhs), RED_THREADS, 0, st>>>((const double2*)a, (size_t)ctx->geom.vol * 12, res,
+                                                                 w->partials, w->counters);
+    check_launch();
+  }
+  QCD_CUDA_CHECK(cudaMemcpyAsync(result, res, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+extern "C" int qcd_cdot(qcd_ctx* ctx, double result[2], const void* a, const void* b, int prec, int nrhs,
+                        void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  QCD_REQUIRE(result && a && b && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_cdot: bad arguments");
+  QCD_REQUIRE(prec == QCD_PREC_SINGLE, QCD_ERR_ARG, "qcd_cdot: SINGLE only");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace* w = workspace(ctx, nrhs, false);
+  double* res = w->dres;
+  {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    k_cdot<<<dim3(w->nblocks, nrhs), RED_THREADS, 0, st>>>((const float4*)a, (const float4*)b, w->v4, res, w->partials,
+                                                          w->counters, w->scal);
+    check_launch();
+  }
+  QCD_CUDA_CHECK(cudaMemcpyAsync(result, res, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int on_device,
+                         const qcd_solve_params* params, qcd_solve_info* info, void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  int result = QCD_OK;
+  API_BEGIN
+  require_operator(ctx);
+  QCD_REQUIRE(x && b && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_solve: bad arguments");
+  qcd_solve_params P;
+  if (params) P = *params;
+  else qcd_solve_params_default(&P);
+  QCD_REQUIRE(P.tol > 0 && P.inner_tol > 0 && P.max_outer >= 1 && P.max_inner >= 1 && P.n_sap >= 0 && P.n_jac >= 1,
+              QCD_ERR_ARG, "qcd_solve: bad parameters");
+  QCD_REQUIRE(P.sap_prec == QCD_PREC_SINGLE || P.sap_prec == QCD_PREC_HALF, QCD_ERR_ARG,
+              "qcd_solve: sap_prec must be SINGLE or HALF");
+  cudaStream_t st = (cudaStream_t)stream;
+  const Geom& g = ctx->geom;
+  Workspace* w = workspace(ctx, nrhs, true);
+  const size_t n2 = (size_t)g.vol * 12;
+  const size_t canon_bytes = (size_t)g.vol * 24 * sizeof(double) * nrhs;
+  const dim3 rgrid(w->nblocks, nrhs);
+  const dim3 sgrid(grid_for(g.vol, 128), nrhs);
+  double* d_red = w->dres;  // [0, nrhs): |b|^2, [nrhs, 2 nrhs): |r|^2, [2 nrhs, 3 nrhs): scale
+  std::vector<double> h_b2(nrhs), h_r2(nrhs), h_scale(nrhs);
+
+  // import b (and the guess), r = b - D x
+  int rc = qcd_import_spinor(ctx, w->b64, b, QCD_PREC_DOUBLE, nrhs, on_device, stream);
+  if (rc != QCD_OK) throw Error{rc, ctx->err};
+  {
+    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+    k_norm2_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, n2, d_red, w->partials, w->counters);
+    check_launch();
+  }
+  if (P.x_is_guess) {
+    rc = qcd_import_spinor(ctx, w->x64, x, QCD_PREC_DOUBLE, nrhs, on_device, stream);
+    if (rc != QCD_OK) throw Error{rc, ctx->err};
+  } else {
+    QCD_CUDA_CHECK(cudaMemsetAsync(w->x64, 0, n2 * sizeof(double2) * nrhs, st));
+  }
+  auto residual = [&]() {
+    dslash_launch(ctx, w->r64, w->x64, QCD_PREC_DOUBLE, MODE_D, nrhs, st);
+    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+    k_residual_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, w->r64, n2, d_red + nrhs, w->partials, w->counters);
+    check_launch();
+    QCD_CUDA_CHECK(cudaMemcpyAsync(h_r2.data(), d_red + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+  };
+  residual();
+  QCD_CUDA_CHECK(cudaMemcpyAsync(h_b2.data(), d_red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+
+  int outer = 0, inner_total = 0, last_inner_status = QCD_OK, breakdowns = 0;
+  double worst_rel = 0.0;
+  auto rel = [&](int r) { return h_b2[r] > 0 ? std::sqrt(h_r2[r] / h_b2[r]) : 0.0; };
+  for (;;) {
+    worst_rel = 0.0;
+    bool finite = true;
+    for (int r = 0; r < nrhs; ++r) {
+      worst_rel = std::max(worst_rel, rel(r));
+      finite = finite && std::isfinite(h_r2[r]);
+    }
+    if (!finite) {
+      result = QCD_ERR_NONFINITE;
+      break;
+    }
+    if (worst_rel < P.tol) break;
+    if (outer >= P.max_outer) {
+      result = last_inner_status == QCD_ERR_BREAKDOWN ? QCD_ERR_BREAKDOWN : QCD_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++outer;
+    // p = R_SP(r / err); the inner right-hand side of A q = C_inv p
+    for (int r = 0; r < nrhs; ++r) h_scale[r] = h_r2[r] > 0 ? 1.0 / std::sqrt(h_r2[r]) : 0.0;
+    QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    {
+      LaunchScope ls(ctx, QCD_KC_BLAS, st);
+      k_f64_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, w->r64, w->tmp32, d_red + 2 * nrhs);
+      check_launch();
+    }
+    clover_apply_launch(ctx, w->tmp32, w->tmp32, QCD_PREC_SINGLE, 1, nrhs, st);
+    int st_inner = QCD_OK;
+    inner_total += bicgstab_sap(ctx, w, w->tmp32, nrhs, P, st, &st_inner);
+    last_inner_status = st_inner;
+    if (st_inner == QCD_ERR_BREAKDOWN) ++breakdowns;
+    if (st_inner == QCD_ERR_NONFINITE) {
+      result = QCD_ERR_NONFINITE;
+      break;
+    }
+    // x += err * P_DP(q)
+    for (int r = 0; r < nrhs; ++r) h_scale[r] = std::sqrt(h_r2[r]);
+    QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    {
+      LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+      k_f64_axpy_f32<<<sgrid, 128, 0, st>>>(g, w->x64, w->x, d_red + 2 * nrhs);
+      check_launch();
+    }
+    residual();
+  }
+  rc = qcd_export_spinor(ctx, x, w->x64, QCD_PREC_DOUBLE, nrhs, on_device, stream);
+  if (rc != QCD_OK) throw Error{rc, ctx->err};
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+  (void)canon_bytes;
+  (void)breakdowns;
+  if (info) {
+    info->outer_iters = outer;
+    info->inner_iters = inner_total;
+    info->status = result;
+    info->true_resid = worst_rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (result != QCD_OK) {
+    ctx->err = result == QCD_ERR_NOT_CONVERGED ? "qcd_solve: tolerance not reached"
+               : result == QCD_ERR_BREAKDOWN   ? "qcd_solve: BiCGStab breakdown"
+                                               : "qcd_solve: non-finite residual";
+    return result;
+  }
+  API_END(ctx)
+}

@@ -1,0 +1,130 @@
+"""GPU parity of the operator kernels against the float64 oracle: D, D^dag,
+A = C_inv D, the clover multiply and its inverse, the domain blocks of A,
+layout round trips; small lattices element by element, the full 32^4 size on
+sampled sites.  Bar: relative L2 <= 1e-6 in float32, 1e-13 in float64."""
+
+import numpy as np
+import pytest
+
+from gpu_util import Problem, rel_l2, to_np
+from lattice_inputs import gaussian_spinor
+from oracle import pointwise
+from oracle.dirac import site_mul
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # dims, domain, bc_t, basis
+    ((8, 8, 8, 8), (4, 4, 4, 4), -1, "chiral"),
+    ((4, 4, 4, 8), (2, 2, 2, 2), -1, "chiral"),
+    ((2, 2, 2, 2), (1, 1, 1, 1), -1, "chiral"),
+    ((8, 4, 4, 16), (4, 2, 2, 4), 1, "chiral"),
+    ((4, 8, 4, 4), (2, 4, 2, 2), -1, "paper"),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "x".join(map(str, c[0])) + f"_d{c[1][0]}{c[1][3]}_{c[3]}")
+def prob(request):
+    dims, domain, bc_t, basis = request.param
+    p = Problem(dims, domain, eps=0.4, kappa=0.12, csw=1.2, seed=1001, bc_t=bc_t, basis=basis)
+    yield p
+    p.close()
+
+
+def test_roundtrip_layouts(prob):
+    x = prob.source(2001)
+    for prec, tol in (("double", 0.0), ("single", 1e-7), ("half", 2e-3)):
+        back = to_np(prob.lat.to_canonical(prob.lat.to_internal(x, prec), prec))
+        err = rel_l2(back, x)
+        assert err <= tol, (prec, err)
+
+
+@pytest.mark.parametrize("prec,tol", [("single", 1e-6), ("double", 1e-13)])
+def test_D_and_Ddag(prob, prec, tol):
+    x = prob.source(2002)
+    got = to_np(prob.lat.apply_D(x, prec))
+    assert rel_l2(got, prob.op.D(x)) <= tol
+    got = to_np(prob.lat.apply_D(x, prec, dagger=True))
+    assert rel_l2(got, prob.op.Ddag(x)) <= tol
+
+
+def test_A(prob):
+    x = prob.source(2003)
+    assert rel_l2(to_np(prob.lat.apply_A(x)), prob.op.A(x)) <= 1e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("single", 1e-6), ("double", 1e-13)])
+def test_clover_and_inverse(prob, prec, tol):
+    x = prob.source(2004)
+    got = to_np(prob.lat.apply_clover(x, prec, inverse=False))
+    assert rel_l2(got, x + site_mul(prob.op.c, x)) <= tol
+    got = to_np(prob.lat.apply_clover(x, prec, inverse=True))
+    assert rel_l2(got, prob.op.apply_cinv(x)) <= tol
+
+
+def test_domain_blocks(prob):
+    x = prob.source(2005)
+    for row in (0, 1):
+        for col in (0, 1):
+            got = to_np(prob.lat.apply_A_block(x, row, col))
+            ref = prob.op.A_block(x, row, col)
+            assert rel_l2(got, ref) <= 1e-6, (row, col)
+            # exact zeros on the other colour
+            assert np.abs(got * prob.op.mask(1 - row)).max() == 0
+
+
+def test_multi_rhs_D():
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), seed=1002)
+    try:
+        xs = gaussian_spinor(p.dims, 2006, nrhs=3)
+        got = to_np(p.lat.apply_D(xs, "single", nrhs=3))
+        for r in range(3):
+            assert rel_l2(got[r], p.op.D(xs[r])) <= 1e-6
+    finally:
+        p.close()
+
+
+def test_D_full_size_sampled_32x4():
+    """The 32^4 workload in the launch configuration the benchmark times,
+    checked on 48 sampled sites against the site-by-site oracle."""
+    dims = (32, 32, 32, 32)
+    p = Problem(dims, (4, 4, 4, 4), eps=0.3, kappa=0.125, csw=1.0, seed=1003, oracle=False)
+    try:
+        x = gaussian_spinor(dims, 2007)
+        out32 = to_np(p.lat.apply_D(x, "single"))
+        out64 = to_np(p.lat.apply_D(x, "double"))
+        rng = np.random.default_rng(5)
+        num = den = num64 = 0.0
+        for _ in range(48):
+            c = tuple(int(rng.integers(0, dims[mu])) for mu in range(4))
+            ref = pointwise.D_at(p.u, x, c, 0.125, 1.0, p.gammas, -1)
+            g32 = out32[c[3], c[2], c[1], c[0]]
+            g64 = out64[c[3], c[2], c[1], c[0]]
+            num += np.sum(np.abs(g32 - ref) ** 2)
+            num64 += np.sum(np.abs(g64 - ref) ** 2)
+            den += np.sum(np.abs(ref) ** 2)
+        assert np.sqrt(num / den) <= 1e-6
+        assert np.sqrt(num64 / den) <= 1e-13
+    finally:
+        p.close()
+
+
+def test_set_gauge_rejects_non_su3():
+    from paper_2109_10687_gb300 import binding as B
+    p = Problem((4, 4, 4, 4), (2, 2, 2, 2), seed=1004, oracle=False)
+    try:
+        bad = p.u.copy()
+        bad[0, 0, 0, 0, 0] *= 1.01
+        with pytest.raises(B.QcdError) as e:
+            p.lat.set_gauge(bad, check_tol=1e-10)
+        assert e.value.code == B.QCD_ERR_ARG
+    finally:
+        p.close()
+
+
+def test_bad_geometry_rejected():
+    from paper_2109_10687_gb300 import binding as B
+    with pytest.raises(B.QcdError):
+        B.qcd_create((8, 8, 8, 12), (4, 4, 4, 4))      # 12 is not a multiple of 2*4
+    with pytest.raises(B.QcdError):
+        B.qcd_create((12, 12, 12, 12), (3, 3, 3, 3))   # not a power of two

@@ -1,0 +1,116 @@
+"""GPU solves of D x = b (Algorithms 4 and 5 with SAP) against the float64
+oracle: true residual <= 1e-10 recomputed by the oracle, solution against the
+oracle's own solve, the structure of Algorithm 5 against the oracle's literal
+iterates, batched right-hand sides, failure statuses."""
+
+import numpy as np
+import pytest
+
+from gpu_util import Problem, rel_l2, to_np
+from lattice_inputs import gaussian_spinor, point_source
+from oracle import solvers
+
+pytestmark = pytest.mark.gpu
+
+
+def true_resid(op, x, b):
+    return float(np.linalg.norm((b - op.D(x)).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """8^4, eps 0.3, kappa 0.12, c_SW 1.0, 4^4 domains (the small solve workload)."""
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), eps=0.3, kappa=0.12, csw=1.0, seed=1001)
+    yield p
+    p.close()
+
+
+@pytest.fixture(scope="module")
+def c1_ref(c1):
+    b = gaussian_spinor(c1.dims, 2001)
+    x, _, ok = solvers.bicgstab(c1.op.D, b, 1e-12, 3000)
+    assert ok
+    return b, x
+
+
+@pytest.mark.parametrize("sap_prec", ["single", "half"])
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_solve_to_1e10(c1, c1_ref, sap_prec, use_graph):
+    b, x_ref = c1_ref
+    x, rc, info = c1.lat.solve(b, tol=1e-10, inner_tol=1e-6 if sap_prec == "single" else 1e-5,
+                               n_sap=4, n_jac=4, sap_prec=sap_prec, use_graph=use_graph)
+    x = to_np(x)
+    assert rc == 0
+    assert info.true_resid < 1e-10
+    assert true_resid(c1.op, x, b) < 1e-10
+    assert rel_l2(x, x_ref) < 1e-8
+    assert 1 <= info.outer_iters <= 6
+
+
+def test_solve_host_buffers(c1, c1_ref):
+    b, x_ref = c1_ref
+    x, rc, info = c1.lat.solve(b, host=True, tol=1e-10)
+    assert rc == 0 and isinstance(x, np.ndarray)
+    assert true_resid(c1.op, x, b) < 1e-10
+
+
+def test_algorithm5_iterates_match_oracle(c1):
+    """Three iterations of Algorithm 5 inside one outer step, compared with the
+    oracle's literal Algorithm 5 (x = M_SAP y) after three iterations."""
+    b = gaussian_spinor(c1.dims, 2002)
+    x, rc, info = c1.lat.solve(b, tol=1e-14, inner_tol=1e-30, max_outer=1, max_inner=3, n_sap=2, n_jac=3,
+                               raise_on_error=False)
+    assert info.inner_iters == 3 and info.outer_iters == 1
+    bn = np.linalg.norm(b.ravel())
+    bp = c1.op.apply_cinv(b / bn)
+    x_or, _, it, status = solvers.bicgstab_precdd(c1.op, bp, 2, 3, 1e-30, 3)
+    assert it == 3
+    assert rel_l2(to_np(x), bn * x_or) < 2e-5
+
+
+def test_batched_point_sources(c1):
+    """Several spin-colour point sources in one batched solve."""
+    srcs = np.stack([point_source(c1.dims, c, s) for c, s in ((0, 0), (1, 2), (2, 3))])
+    x, rc, info = c1.lat.solve(srcs, nrhs=3, tol=1e-10)
+    x = to_np(x)
+    assert rc == 0
+    for r in range(3):
+        assert true_resid(c1.op, x[r], srcs[r]) < 1e-10
+
+
+def test_zero_source(c1):
+    z = np.zeros(c1.lat.site_shape + (3, 4), dtype=np.complex128)
+    x, rc, info = c1.lat.solve(z, tol=1e-10)
+    assert rc == 0 and np.abs(to_np(x)).max() == 0 and info.outer_iters == 0
+
+
+def test_nonfinite_source_reports_status(c1):
+    from paper_2109_10687_gb300 import binding as B
+    b = gaussian_spinor(c1.dims, 2003)
+    b[1, 2, 3, 4, 0, 0] = np.nan
+    x, rc, info = c1.lat.solve(b, tol=1e-10, raise_on_error=False)
+    assert rc == B.QCD_ERR_NONFINITE
+
+
+def test_iteration_limit_reports_status(c1):
+    from paper_2109_10687_gb300 import binding as B
+    b = gaussian_spinor(c1.dims, 2004)
+    x, rc, info = c1.lat.solve(b, tol=1e-12, max_outer=1, max_inner=1, raise_on_error=False)
+    assert rc == B.QCD_ERR_NOT_CONVERGED
+    assert info.outer_iters == 1
+
+
+def test_resume_from_guess(c1, c1_ref):
+    """A solve started from a previous iterate (x_is_guess) needs fewer steps."""
+    b, x_ref = c1_ref
+    x0, rc, _ = c1.lat.solve(b, tol=1e-6)
+    from paper_2109_10687_gb300 import binding as B
+    p = B.qcd_solve_params_default()
+    p.x_is_guess = 1
+    p.tol = 1e-10
+    import torch
+    src = torch.view_as_real(torch.from_numpy(b).cuda()).contiguous()
+    out = torch.view_as_real(x0.contiguous()).contiguous().clone()
+    rc, info = B.qcd_solve(c1.lat.ctx, out, src, 1, p)
+    assert rc == 0
+    assert true_resid(c1.op, to_np(torch.view_as_complex(out)), b) < 1e-10

@@ -198,3 +198,20 @@ def test_paper_form_of_A():
         cinv_blk[12 * i:12 * i + 12, 12 * i:12 * i + 12] = cinv[i]
     x = gaussian_spinor(dims, 82)
     assert np.allclose(op.A(x).ravel(), cinv_blk @ mat_d @ x.ravel(), atol=1e-12)
+
+
+def test_pointwise_matches_whole_lattice():
+    """The site-by-site form used for sampled checks of large lattices equals
+    the whole-lattice operator."""
+    from oracle import pointwise
+    dims = (4, 4, 2, 6)
+    for basis, g in (("paper", gamma_paper()), ("chiral", gamma_chiral())):
+        u = random_su3_field(dims, 0.5, 91)
+        op = CloverWilson(u, 0.13, 1.2, g, bc_t=-1)
+        x = gaussian_spinor(dims, 92)
+        full = op.D(x)
+        rng = np.random.default_rng(3)
+        for _ in range(12):
+            c = tuple(int(rng.integers(0, dims[mu])) for mu in range(4))
+            got = pointwise.D_at(u, x, c, 0.13, 1.2, g, -1)
+            assert np.allclose(got, full[c[3], c[2], c[1], c[0]], atol=1e-12)
