@@ -355,6 +355,7 @@ extern "C" int qcd_destroy(qcd_ctx* ctx) {
                   ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   delete ctx->prof;
   delete ctx;
   return QCD_OK;

@@ -521,6 +521,7 @@ struct qcd_ctx {
   float4* cinv32 = nullptr;
   __half2* cinv16 = nullptr;
   int* d_status = nullptr;       // device status word (non-finite, ...)
+  cudaStream_t aux_stream = nullptr;  // private stream for graph capture
   qcd::Workspace* ws = nullptr;
   qcd::Profiler* prof = nullptr;
   long long launches = 0;

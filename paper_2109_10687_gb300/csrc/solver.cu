@@ -683,6 +683,14 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   QCD_REQUIRE(P.sap_prec == QCD_PREC_SINGLE || P.sap_prec == QCD_PREC_HALF, QCD_ERR_ARG,
               "qcd_solve: sap_prec must be SINGLE or HALF");
   cudaStream_t st = (cudaStream_t)stream;
+  if (P.use_graph) {
+    // stream capture is not possible on the legacy default stream: run the
+    // solve on a private stream, ordered after the caller's stream
+    if (!ctx->aux_stream) QCD_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+    QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+    st = ctx->aux_stream;
+    stream = (void*)st;
+  }
   const Geom& g = ctx->geom;
   Workspace* w = workspace(ctx, nrhs, true);
   const size_t n2 = (size_t)g.vol * 12;
