@@ -30,6 +30,8 @@ class Lattice:
         self.domain = tuple(int(v) for v in domain)
         self.device = torch.device(device)
         if self.device.type == "cuda":
+            if self.device.index is None:
+                self.device = torch.device("cuda", torch.cuda.current_device())
             torch.cuda.set_device(self.device)
         basis_code = B.BASIS_CHIRAL if basis == "chiral" else B.BASIS_PAPER
         self.ctx = B.qcd_create(self.dims, self.domain, bc_t, basis_code)
