@@ -1,0 +1,410 @@
+"""Benchmark: mixed-precision SAP-BiCGStab solve of D x = b to float64 true
+residual 1e-10 on a 32^4 lattice, plus the float32 Dslash roofline and the
+plain float32 SAP-BiCGStab time on the same GB300.
+
+One step = one complete solve (import of b, defect-correction loop with
+float16-storage SAP + float32 BiCGStab + float64 residuals, export of x) of
+the 32^4 workload: eps = 0.3 gauge field, kappa = 0.125, c_SW = 1.0, one
+Gaussian source, 4^4 domains, n_sap = 4, n_jac = 4.  Every step works on
+inputs far larger than L2 (the float32 links and clover alone are 600 MB).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun) every rank solves its own replica (weak scaling, no
+collective on the data path); the timed region is bracketed by a barrier.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GB/s vs HBM roofline; SAP-BiCGStab time to FP64 resid 1e-10 vs plain FP32"
+DIMS = (32, 32, 32, 32)
+DOMAIN = (4, 4, 4, 4)
+EPS, KAPPA, CSW = 0.3, 0.125, 1.0
+N_SAP, N_JAC = 4, 4
+GAUGE_SEED, SOURCE_SEED = 1001, 2001
+WORKLOAD = ("32^4 lattice, periodic space / antiperiodic time, chiral basis, U = exp(i 0.3 H) "
+            "(seeded), kappa 0.125, c_sw 1.0, one Gaussian source; float16-storage SAP "
+            "(4^4 domains, n_sap 4, n_jac 4) + float32 BiCGStab + float64 defect correction "
+            "to true residual 1e-10")
+D_BYTES_PER_SITE = 96 + 96 + 4 * 72 + 288          # in + out spinor, 4 links (18 reals), clover
+D_FLOP_PER_SITE = 1824
+
+
+def sap_bytes_per_site(prec):
+    """Algorithmic bytes per site of one SAP half-sweep launch, averaged over
+    the launches of one M_SAP (n_sap + 1 sweeps, two colours):
+    read s, b, own links, C_inv, the neighbouring domains' x across the
+    surface (2 sites per site for 4^4 domains) and the crossing backward links
+    (1 per site); write x and s."""
+    sp = 96 if prec == "single" else 52
+    link = 72 if prec == "single" else 36
+    clov = 288 if prec == "single" else 144
+    base = sp + 4 * link + clov + sp                    # s in, links, C_inv, x out
+    surf = 2 * sp + link                                # halo spinors + crossing links
+    upd = 96 + sp                                       # b (float32) in, s out
+    seq = []
+    for sweep in range(N_SAP + 1):
+        last = sweep == N_SAP
+        for colour in (0, 1):
+            has_surf = not (sweep == 0 and colour == 0)
+            seq.append(base + (surf if has_surf else 0) + (0 if last else upd))
+    return sum(seq) / len(seq)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+# Inner (Algorithm 5) iterations and outer (Algorithm 4) steps the 32^4 solve
+# takes on the GPU path; the oracle leg scales its measured per-iteration cost
+# by these counts (an extrapolation, stated in the output).
+DEFAULT_ITERS = {"inner": 16, "outer": 3}
+
+
+SAMPLE_DIMS = (8, 8, 16, 16)
+
+
+def oracle_sample(seconds_budget=20.0, iters=None, max_apps=3):
+    """Time the float64 oracle's A M_SAP (Algorithm 3) on an 8x8x16x16
+    sub-volume of the same recipe and scale to one 32^4 solve."""
+    import oracle.sap as osap
+    from lattice_inputs import gaussian_spinor, random_su3_field
+    from oracle.dirac import CloverWilson
+    from oracle.gamma import gamma_chiral
+    iters = iters or DEFAULT_ITERS
+    dims = SAMPLE_DIMS
+    u = random_su3_field(dims, EPS, GAUGE_SEED)
+    op = CloverWilson(u, KAPPA, CSW, gamma_chiral(), bc_t=-1, domain=DOMAIN)
+    b = gaussian_spinor(dims, SOURCE_SEED)
+    n_am = 0
+    t0 = time.perf_counter()
+    while True:
+        osap.am_sap(op, b, N_SAP, N_JAC)
+        n_am += 1
+        if time.perf_counter() - t0 > seconds_budget or n_am >= max_apps:
+            break
+    t_am = (time.perf_counter() - t0) / n_am
+    vol_ratio = np.prod(DIMS) / np.prod(dims)
+    # one Algorithm-5 iteration = 2 A M_SAP applies (+ vector work, not counted);
+    # each outer step adds one more M_SAP for the final x = M_SAP y
+    n_am_solve = 2 * iters["inner"] + iters["outer"]
+    t_solve = t_am * vol_ratio * n_am_solve
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or 1
+    return {
+        "value": 1.0 / t_solve,
+        "unit": "solves/s",
+        "cores": threads,
+        "host_cores": cores,
+        "kind": "oracle",
+        "sample": (f"{n_am} float64 oracle A*M_SAP applications (Algorithm 3, n_sap {N_SAP}, n_jac {N_JAC}) on an "
+                   f"8x8x16x16 lattice of the same recipe, {t_am:.2f} s each, scaled by the volume ratio {vol_ratio:.0f} "
+                   f"and by {n_am_solve} applications per 32^4 solve ({iters['inner']} inner iterations, "
+                   f"{iters['outer']} outer steps)"),
+        "seconds_per_am_sap_sample": t_am,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass  # the oracle has nothing to warm up; each step is a fresh bounded sample
+    vals = []
+    t0 = time.perf_counter()
+    info = None
+    for _ in range(args.steps):
+        info = oracle_sample(seconds_budget=5.0, max_apps=1)
+        vals.append(info["value"])
+    elapsed = time.perf_counter() - t0
+    value = statistics.median(vals)
+    cpu = dict(info)
+    cpu["value"] = value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "parallelism": "replicas"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": elapsed,
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from lattice_inputs import gaussian_spinor, random_su3_field
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300 import build as _build
+    from paper_2109_10687_gb300.lattice import Lattice
+
+    _build.build()
+    dev = torch.device("cuda", local)
+    u = random_su3_field(DIMS, EPS, GAUGE_SEED + rank)
+    b_np = gaussian_spinor(DIMS, SOURCE_SEED + rank)
+    lat = Lattice(DIMS, DOMAIN, -1, "chiral", dev).setup(u, KAPPA, CSW)
+    del u
+    b_dev = torch.view_as_real(torch.from_numpy(b_np)).to(dev).contiguous()
+    x_dev = torch.zeros_like(b_dev)
+
+    def params(sap_prec, graph=1):
+        p = B.qcd_solve_params_default()
+        p.tol, p.n_sap, p.n_jac = 1e-10, N_SAP, N_JAC
+        p.sap_prec = B.PREC_HALF if sap_prec == "half" else B.PREC_SINGLE
+        p.inner_tol = 1e-5 if sap_prec == "half" else 1e-6
+        p.max_inner = 1000
+        p.use_graph = graph
+        return p
+
+    P_MIX = params("half")
+    P_F32 = params("single")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def solve(p, xb=x_dev, bb=b_dev):
+        rc, info = B.qcd_solve(lat.ctx, xb, bb, 1, p)
+        return info
+
+    # warm-up
+    for _ in range(args.warmup):
+        info = solve(P_MIX)
+    # timed region: K full solves, kernel-class device time measured live
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_index = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    B.qcd_profile_read(lat.ctx, B.KC_SAP_BLOCK, reset=True)
+    for kc in range(5):
+        B.qcd_profile_read(lat.ctx, kc, reset=True)
+    launches0 = B.qcd_launch_count(lat.ctx)
+    P_PROF = params("half", graph=0)   # events bracket every launch; no graph
+    B.qcd_profile_enable(lat.ctx, True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record()
+    infos = []
+    for _ in range(args.steps):
+        infos.append(solve(P_PROF))
+    ev1.record()
+    barrier()
+    wall = time.perf_counter() - t0
+    B.qcd_profile_enable(lat.ctx, False)
+    launches = B.qcd_launch_count(lat.ctx) - launches0
+    clk = clocks.stop()
+    dev_ms = ev0.elapsed_time(ev1)
+    elapsed = max(dev_ms / 1000.0, 0.0)
+    prof = {kc: B.qcd_profile_read(lat.ctx, kc, reset=True) for kc in range(5)}
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    ms_per_step = 1000.0 * elapsed / args.steps
+
+    # graph-replayed solve time (the production setting), same workload
+    barrier()
+    tg = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        solve(P_MIX)
+    barrier()
+    graph_ms = 1000.0 * (time.perf_counter() - tg) / max(1, args.steps // 2)
+
+    # plain float32 SAP-BiCGStab (same defect correction), the comparison arm
+    barrier()
+    tf = time.perf_counter()
+    info_f32 = solve(P_F32)
+    barrier()
+    f32_ms = 1000.0 * (time.perf_counter() - tf)
+
+    # Dslash: float32 D on the 32^4 field, CUDA events on the launching stream
+    a32 = lat.field("single")
+    o32 = lat.field("single")
+    B.qcd_import_spinor(lat.ctx, a32, b_dev, B.PREC_SINGLE)
+    for _ in range(5):
+        B.qcd_apply_D(lat.ctx, o32, a32, B.PREC_SINGLE)
+    nrep = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(nrep):
+        B.qcd_apply_D(lat.ctx, o32, a32, B.PREC_SINGLE)
+    e1.record()
+    torch.cuda.synchronize()
+    d_ms = e0.elapsed_time(e1) / nrep
+    vol = int(np.prod(DIMS))
+    peak, peak_kind = measured_peaks()
+    d_gbs = D_BYTES_PER_SITE * vol / (d_ms * 1e-3) / 1e9
+    d_gflops = D_FLOP_PER_SITE * vol / (d_ms * 1e-3) / 1e9
+
+    # end to end through the public call with host buffers (pinned)
+    b_host = torch.from_numpy(b_np.view(np.float64).reshape(b_dev.shape)).pin_memory()
+    x_host = torch.zeros_like(b_host).pin_memory()
+    barrier()
+    te = time.perf_counter()
+    ne = max(1, args.steps // 2)
+    for _ in range(ne):
+        rc, _ = B.qcd_solve(lat.ctx, x_host, b_host, 1, P_MIX)
+    barrier()
+    e2e_s = (time.perf_counter() - te) / ne
+    e2e_value = world / e2e_s
+
+    # dominant kernel by device time in the timed region
+    sap_n, sap_ms = prof[B.KC_SAP_BLOCK]
+    total_ms = sum(v[1] for v in prof.values())
+    sap_avg_ms = sap_ms / max(1, sap_n)
+    sap_bytes = sap_bytes_per_site("half") * vol / 2
+    sap_gbs = sap_bytes / (sap_avg_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "sap_block_traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as fh:
+            traffic = json.load(fh).get("bytes_per_launch_32x4")
+
+    inner = int(np.median([i.inner_iters for i in infos]))
+    outer = int(np.median([i.outer_iters for i in infos]))
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "precision": {"sap_storage": "f16", "krylov": "f32", "correction": "f64"},
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "domain": list(DOMAIN), "n_sap": N_SAP,
+                   "n_jac": N_JAC, "tol": 1e-10, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (links + clover + vectors > 1 GB)"},
+        "time_to_solution_ms": ms_per_step,
+        "time_to_solution_graph_ms": graph_ms,
+        "iterations": {"inner": inner, "outer": outer},
+        "true_resid": max(i.true_resid for i in infos),
+        "plain_fp32": {"time_to_solution_ms": f32_ms, "inner": info_f32.inner_iters, "outer": info_f32.outer_iters,
+                       "true_resid": info_f32.true_resid, "speedup_of_mixed": f32_ms / graph_ms},
+        "dslash": {"kernel": "dslash_kernel<float, D>", "ms": d_ms, "gbs": d_gbs, "gflops": d_gflops,
+                   "bytes_per_site": D_BYTES_PER_SITE, "flop_per_site": D_FLOP_PER_SITE,
+                   "frac_of_hbm": d_gbs / peak, "peak_gbs": peak, "peak_kind": peak_kind},
+        "roofline": {"kernel": "sap_block_kernel<F16>", "bound": "hbm", "achieved": sap_gbs, "peak": peak,
+                     "unit": "GB/s", "frac": sap_gbs / peak, "traffic": traffic,
+                     "bytes_per_site": sap_bytes_per_site("half"), "sites_per_launch": vol // 2,
+                     "avg_launch_ms": sap_avg_ms, "share_of_device_time": sap_ms / total_ms if total_ms else None,
+                     "peak_kind": peak_kind},
+        "kernel_classes_ms": {name: prof[k][1] for k, name in
+                              ((B.KC_DSLASH, "dslash_A"), (B.KC_SAP_BLOCK, "sap_block"), (B.KC_BLAS, "blas"),
+                               (B.KC_DOUBLE, "float64"), (B.KC_OTHER, "other"))},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(b_host.numel() * 8),
+                "d2h_bytes_per_step": int(x_host.numel() * 8)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(iters={"inner": inner, "outer": outer})
+    if rank == 0:
+        print(json.dumps(line))
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
