@@ -212,6 +212,32 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
+def run_kernel_case(args):
+    """Small profiling case: one kernel family applied REPS times on an L^4
+    lattice of the benchmark recipe (for ncu captures; prints nothing timed)."""
+    import torch
+    from lattice_inputs import gaussian_spinor, random_su3_field
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300.lattice import Lattice
+    torch.cuda.set_device(0)
+    dims = (args.lattice,) * 4
+    lat = Lattice(dims, DOMAIN, -1, "chiral", "cuda:0").setup(random_su3_field(dims, EPS, GAUGE_SEED), KAPPA, CSW)
+    b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, SOURCE_SEED))).cuda().contiguous()
+    prec = B.PREC_DOUBLE if args.kernel == "dslash64" else B.PREC_SINGLE
+    a = lat.field("double" if prec == B.PREC_DOUBLE else "single")
+    o = lat.field("double" if prec == B.PREC_DOUBLE else "single")
+    B.qcd_import_spinor(lat.ctx, a, b, prec)
+    for _ in range(args.reps):
+        if args.kernel.startswith("sap"):
+            sp = B.PREC_HALF if args.kernel == "sap16" else B.PREC_SINGLE
+            B.qcd_sap_apply(lat.ctx, o, a, N_SAP, N_JAC, sp, 0)
+        else:
+            B.qcd_apply_D(lat.ctx, o, a, prec)
+    torch.cuda.synchronize()
+    print(f"kernel case {args.kernel} on {dims}: {args.reps} applications done")
+    lat.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,9 +245,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["sap16", "sap32", "dslash", "dslash64"], default=None,
+                    help="profiling case: set up the workload and run only REPS applications of one kernel")
+    ap.add_argument("--lattice", type=int, default=32, help="lattice extent of the profiling case")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.kernel:
+        run_kernel_case(args)
         return
 
     import torch
