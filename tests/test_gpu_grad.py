@@ -35,3 +35,29 @@ def test_grad_matches_oracle(dims, domain, csw):
         assert rel_l2(to_np(torch.view_as_complex(gu)), pi_ref) < 1e-5
     finally:
         p.close()
+
+
+def test_autograd_function_matches_oracle():
+    """torch.autograd through the library solve: L = Re(eta^dag D^-1 b),
+    gradients with respect to b and U against the float64 oracle."""
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300.autograd import solve
+    p = Problem((4, 4, 4, 8), (2, 2, 2, 2), eps=0.3, kappa=0.12, csw=1.0, seed=3100)
+    try:
+        eta, b = p.source(3101), p.source(3102)
+        lam_ref, g_ref = grad.gradients(p.op, eta, b, tol=1e-13)
+        dev = p.lat.device
+        bt = torch.from_numpy(b).to(dev).requires_grad_(True)
+        ut = torch.from_numpy(p.u).to(dev).requires_grad_(True)
+        et = torch.from_numpy(eta).to(dev)
+        params = B.qcd_solve_params_default()
+        params.tol = 1e-12
+        x = solve(bt, ut, p.lat, 0.12, 1.0, params)
+        loss = torch.sum(torch.conj(et) * x).real
+        loss.backward()
+        x_ref = grad.solve_D(p.op, b)
+        assert abs(loss.item() - np.vdot(eta.ravel(), x_ref.ravel()).real) < 1e-9 * abs(loss.item())
+        assert rel_l2(to_np(bt.grad), lam_ref) < 1e-9
+        assert rel_l2(to_np(ut.grad), g_ref) < 1e-5
+    finally:
+        p.close()
