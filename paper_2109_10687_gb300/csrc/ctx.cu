@@ -332,12 +332,16 @@ extern "C" int qcd_create(const int dims[4], const int domain[4], int bc_t, int 
     }
     QCD_CUDA_CHECK(cudaMalloc(&ctx->d_nbr, nbr.size() * sizeof(int)));
     QCD_CUDA_CHECK(cudaMemcpy(ctx->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    QCD_CUDA_CHECK(cudaMalloc(&ctx->d_lex2dom, id_of_lex.size() * sizeof(int)));
+    QCD_CUDA_CHECK(cudaMemcpy(ctx->d_lex2dom, id_of_lex.data(), id_of_lex.size() * sizeof(int),
+                              cudaMemcpyHostToDevice));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->d_tflag, tflag.size()));
     QCD_CUDA_CHECK(cudaMemcpy(ctx->d_tflag, tflag.data(), tflag.size(), cudaMemcpyHostToDevice));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->d_status, 64));
     QCD_CUDA_CHECK(cudaMemset(ctx->d_status, 0, 64));
     g.nbr = ctx->d_nbr;
     g.tflag = ctx->d_tflag;
+    g.lex2dom = ctx->d_lex2dom;
     ctx->prof = new Profiler();
   } catch (const qcd::Error& e) {
     g_create_error = e.msg;
@@ -351,8 +355,9 @@ extern "C" int qcd_create(const int dims[4], const int domain[4], int bc_t, int 
 extern "C" int qcd_destroy(qcd_ctx* ctx) {
   if (!ctx) return QCD_OK;
   workspace_free(ctx);
-  void* ptrs[] = {ctx->d_nbr, ctx->d_tflag, ctx->u64, ctx->u32, ctx->u16, ctx->clov64,
-                  ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status};
+  void* ptrs[] = {ctx->d_nbr, ctx->d_lex2dom, ctx->d_tflag, ctx->u64, ctx->u32, ctx->u16, ctx->clov64,
+                  ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status,
+                  ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
@@ -430,6 +435,7 @@ extern "C" int qcd_build_clover(qcd_ctx* ctx, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   QCD_CUDA_CHECK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   build_clover_launch(ctx, st);
+  build_sap_staging(ctx, st);
   int hs = 0;
   QCD_CUDA_CHECK(cudaMemcpyAsync(&hs, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   QCD_CUDA_CHECK(cudaStreamSynchronize(st));

@@ -86,7 +86,10 @@ __global__ void __launch_bounds__(128) dslash_kernel(Geom g, typename Prec<R>::S
                                                      typename Prec<R>::LP U, typename Prec<R>::CP clov, R kappa) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= g.vol) return;
-  const int dom = (int)(gid >> g.logvd);
+  // domains are visited in lexicographic order, so that the neighbouring
+  // domains whose surface spinors a domain reads are processed at about the
+  // same time and their data is still in L2
+  const int dom = __ldg(g.lex2dom + (int)(gid >> g.logvd));
   const int s = (int)(gid & (g.vd - 1));
   const int rhs_off = blockIdx.y * g.ndom;
   Spinor<R> acc;

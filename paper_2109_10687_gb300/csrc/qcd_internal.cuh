@@ -55,6 +55,7 @@ struct Geom {
   int bc_t;        // +1 periodic, -1 antiperiodic in t
   const int* nbr;  // [ndom][8]: neighbour domain across face 2 mu (+) / 2 mu + 1 (-)
   const unsigned char* tflag;  // [ndom]: bit k set when face k crosses t = Lt-1 <-> 0
+  const int* lex2dom;          // [ndom]: lexicographic domain index -> storage index
 };
 
 // Neighbouring site of (dom, s) in direction mu, forward (fwd) or backward.
@@ -511,6 +512,7 @@ struct qcd_ctx {
   bool have_gauge = false, have_clover = false;
   // device arrays owned by the context
   int* d_nbr = nullptr;
+  int* d_lex2dom = nullptr;
   unsigned char* d_tflag = nullptr;
   double2* u64 = nullptr;
   float2* u32 = nullptr;
@@ -522,6 +524,12 @@ struct qcd_ctx {
   __half2* cinv16 = nullptr;
   int* d_status = nullptr;       // device status word (non-finite, ...)
   cudaStream_t aux_stream = nullptr;  // private stream for graph capture
+  // staging layouts of the shared-memory SAP kernel (4^4 domains only)
+  void* st_link16 = nullptr;
+  void* st_link32 = nullptr;
+  void* st_clov16 = nullptr;
+  void* st_clov32 = nullptr;
+  bool force_generic_sap = false;  // testing: use the generic SAP kernel
   qcd::Workspace* ws = nullptr;
   qcd::Profiler* prof = nullptr;
   long long launches = 0;
@@ -581,6 +589,12 @@ void clover_apply_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int 
                          cudaStream_t st);
 void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col, cudaStream_t st);
 void build_clover_launch(qcd_ctx* ctx, cudaStream_t st);
+void build_sap_staging(qcd_ctx* ctx, cudaStream_t st);
+bool sap_staged_available(const qcd_ctx* ctx);
+void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int n_sap,
+                             int n_jac, cudaStream_t st);
+void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int n_sap,
+                             int n_jac, cudaStream_t st);
 void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
 
 // dslash modes

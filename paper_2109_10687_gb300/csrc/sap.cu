@@ -265,10 +265,14 @@ static void sap_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spinor b
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int n_sap, int n_jac, int sap_prec, void* ws_s,
                       void* ws_x16, void* ws_b16, cudaStream_t st) {
   const Geom& g = ctx->geom;
+  const bool staged = sap_staged_available(ctx) && !ctx->force_generic_sap;
   if (sap_prec == QCD_PREC_SINGLE) {
     F32Spinor xs{x}, bs{(float4*)b}, ss{(float4*)ws_s};
-    sap_sequence<F32Spinor, LinkPtr<float>, CloverPtrF32, CloverBlockF32>(
-        ctx, bs, ss, xs, bs, LinkPtr<float>{ctx->u32}, CloverPtrF32{ctx->cinv32}, n_sap, n_jac, st);
+    if (staged)
+      sap_staged_sequence_f32(ctx, bs, ss, xs, bs, n_sap, n_jac, st);
+    else
+      sap_sequence<F32Spinor, LinkPtr<float>, CloverPtrF32, CloverBlockF32>(
+          ctx, bs, ss, xs, bs, LinkPtr<float>{ctx->u32}, CloverPtrF32{ctx->cinv32}, n_sap, n_jac, st);
   } else {
     const size_t v = (size_t)g.vol;
     F16Spinor s16{(uint4*)ws_s, (float*)((uint4*)ws_s + 3 * v)};
@@ -279,9 +283,12 @@ void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int n_sap, int n
       f32_to_f16_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g, b16, F32Spinor{(float4*)b});
       check_launch();
     }
-    sap_sequence<F16Spinor, LinkPtrHalf, CloverPtrF16, CloverBlockF32>(
-        ctx, b16, s16, x16, F32Spinor{(float4*)b}, LinkPtrHalf{ctx->u16}, CloverPtrF16{ctx->cinv16}, n_sap, n_jac,
-        st);
+    if (staged)
+      sap_staged_sequence_f16(ctx, b16, s16, x16, F32Spinor{(float4*)b}, n_sap, n_jac, st);
+    else
+      sap_sequence<F16Spinor, LinkPtrHalf, CloverPtrF16, CloverBlockF32>(
+          ctx, b16, s16, x16, F32Spinor{(float4*)b}, LinkPtrHalf{ctx->u16}, CloverPtrF16{ctx->cinv16}, n_sap, n_jac,
+          st);
     {
       LaunchScope ls(ctx, QCD_KC_BLAS, st);
       f16_to_f32_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g, F32Spinor{x}, x16);

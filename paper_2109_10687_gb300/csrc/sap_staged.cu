@@ -1,0 +1,428 @@
+// SAP half-sweep kernel for 4^4 domains with the domain's links and C_inv
+// staged in shared memory by bulk asynchronous copies (Sec. 3 of
+// arXiv:2109.10687, Algorithms 1 and 2; the arithmetic is that of
+// sap.cu's generic kernel).
+//
+// One CTA per domain, one thread per site, the domain shape fixed at compile
+// time (strides 1, 4, 16, 64).  At entry one thread arms an mbarrier and
+// issues two cp.async.bulk copies: the domain's links and its C_inv, each a
+// contiguous block of a staging layout built for this kernel.  While they
+// are in flight the threads read their s and evaluate the surface hops from
+// global memory; they then wait (bounded) on the barrier and run every
+// Jacobi sweep and the residual update from shared memory:
+//
+//   staging layouts per domain (global = shared):
+//     links  f16: __half2 [mu 4][site 256][9]     36 B per link, 32-bit reads
+//            f32: float2  [mu 4][site 256][9]     72 B per link, 64-bit reads
+//     C_inv  f16: uint4   [site 256][11]          two blocks of 40 halves + pad
+//            f32: float4  [site 256][19]          two blocks of 36 floats + pad
+//   (the site strides 36/72 B and 176/304 B make each warp's reads free of
+//   shared-memory bank conflicts)
+//
+// Shared memory: f16 104 KB (two CTAs per SM), f32 172 KB (one CTA per SM).
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+constexpr int ST_THREADS = 256;
+constexpr int C16_U4 = 11;   // uint4 per site, f16 C_inv
+constexpr int C32_F4 = 19;   // float4 per site, f32 C_inv
+
+template <bool HALF>
+struct StageT;
+
+template <>
+struct StageT<true> {
+  static constexpr int LINK_BYTES = 4 * 256 * 9 * 4;       // 36864
+  static constexpr int CLOV_BYTES = 256 * C16_U4 * 16;     // 45056
+  using SIO = F16Spinor;
+  __device__ static SU3<float> link(const unsigned char* base, int mu, int site) {
+    const __half2* p = reinterpret_cast<const __half2*>(base) + (mu * 256 + site) * 9;
+    SU3<float> u;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float2 v = __half22float2(p[e]);
+      u.m[e / 3][e % 3] = make_cx(v.x, v.y);
+    }
+    return u;
+  }
+  __device__ static void clover_block(const unsigned char* base, int site, int b, CloverBlockF32& blk) {
+    const uint4* p = reinterpret_cast<const uint4*>(base) + site * C16_U4;
+    // block b occupies halves [40 b, 40 b + 36)
+    const __half2* h = reinterpret_cast<const __half2*>(p) + 20 * b;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      const float2 v = __half22float2(h[k]);
+      blk.r[2 * k] = v.x;
+      blk.r[2 * k + 1] = v.y;
+    }
+  }
+};
+
+template <>
+struct StageT<false> {
+  static constexpr int LINK_BYTES = 4 * 256 * 9 * 8;       // 73728
+  static constexpr int CLOV_BYTES = 256 * C32_F4 * 16;     // 77824
+  using SIO = F32Spinor;
+  __device__ static SU3<float> link(const unsigned char* base, int mu, int site) {
+    const float2* p = reinterpret_cast<const float2*>(base) + (mu * 256 + site) * 9;
+    SU3<float> u;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float2 v = p[e];
+      u.m[e / 3][e % 3] = make_cx(v.x, v.y);
+    }
+    return u;
+  }
+  __device__ static void clover_block(const unsigned char* base, int site, int b, CloverBlockF32& blk) {
+    const float4* p = reinterpret_cast<const float4*>(base) + site * C32_F4 + 9 * b;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = p[k];
+      blk.r[4 * k] = v.x; blk.r[4 * k + 1] = v.y; blk.r[4 * k + 2] = v.z; blk.r[4 * k + 3] = v.w;
+    }
+  }
+};
+
+template <bool HALF>
+struct StagedArgs {
+  Geom g;
+  int colour, n_jac, do_surface, do_update;
+  float kappa;
+  typename StageT<HALF>::SIO s_in, s_out, x;
+  F32Spinor b;
+  const unsigned char* links;  // staging layout, all domains
+  const unsigned char* clov;
+  int* status;                 // word 0: set to QCD_ERR_TIMEOUT if a wait gives up
+};
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: about 2^22 polls (each try_wait itself suspends for a while);
+// returns false when it gives up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// hops
+// ---------------------------------------------------------------------------
+// local coordinates of a 4^4 site: x = s & 3, y = (s >> 2) & 3, z = (s >> 4) & 3, t = s >> 6
+template <int MU>
+__device__ __forceinline__ int lc(int s) { return (s >> (2 * MU)) & 3; }
+
+// shared-memory x: float4 group k holds complex components 2k and 2k+1,
+// component c = spin * 3 + colour
+__device__ __forceinline__ void st_load_x(const float4* sx, int site, Spinor<float>& p) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 v = sx[k * 256 + site];
+    p.v[(2 * k) / 3][(2 * k) % 3] = make_cx(v.x, v.y);
+    p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v.z, v.w);
+  }
+}
+
+// acc += both intra-domain hops of direction MU (operand x from shared memory)
+template <int MU, bool HALF>
+__device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* sl, int s, Spinor<float>& acc) {
+  constexpr int step = 1 << (2 * MU);
+  const int c = lc<MU>(s);
+  if (c < 3) {
+    Spinor<float> p;
+    st_load_x(sx, s + step, p);
+    HalfSpinor<float> h, uh;
+    project<MU, -1>(p, h);
+    const SU3<float> u = StageT<HALF>::link(sl, MU, s);
+    su3_mul(u, h, uh);
+    accumulate<MU, -1>(acc, uh);
+  }
+  if (c > 0) {
+    Spinor<float> p;
+    st_load_x(sx, s - step, p);
+    HalfSpinor<float> h, uh;
+    project<MU, +1>(p, h);
+    const SU3<float> u = StageT<HALF>::link(sl, MU, s - step);
+    su3_dag_mul(u, h, uh);
+    accumulate<MU, +1>(acc, uh);
+  }
+}
+
+// acc += both domain-leaving hops of direction MU (operand x and links from memory)
+template <int MU, bool HALF, typename SIO>
+__device__ __forceinline__ void st_inter(const Geom& g, const SIO& x, const unsigned char* links, int dom, int s,
+                                         Spinor<float>& acc) {
+  constexpr int step = 1 << (2 * MU);
+  const int c = lc<MU>(s);
+  constexpr size_t dom_bytes = StageT<HALF>::LINK_BYTES;
+  if (c == 3) {
+    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU);
+    const int sign = ((__ldg(g.tflag + dom) >> (2 * MU)) & 1) ? g.bc_t : 1;
+    Spinor<float> p;
+    x.load(g, nd, s - 3 * step, p);
+    HalfSpinor<float> h, uh;
+    project<MU, -1>(p, h);
+    const SU3<float> u = StageT<HALF>::link(links + dom * dom_bytes, MU, s);
+    su3_mul(u, h, uh);
+    if (sign < 0) scale_half(uh, -1.0f);
+    accumulate<MU, -1>(acc, uh);
+  }
+  if (c == 0) {
+    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU + 1);
+    const int sign = ((__ldg(g.tflag + dom) >> (2 * MU + 1)) & 1) ? g.bc_t : 1;
+    const int ns = s + 3 * step;
+    Spinor<float> p;
+    x.load(g, nd, ns, p);
+    HalfSpinor<float> h, uh;
+    project<MU, +1>(p, h);
+    const SU3<float> u = StageT<HALF>::link(links + nd * dom_bytes, MU, ns);
+    su3_dag_mul(u, h, uh);
+    if (sign < 0) scale_half(uh, -1.0f);
+    accumulate<MU, +1>(acc, uh);
+  }
+}
+
+template <bool HALF>
+__device__ __forceinline__ void st_clover(const unsigned char* sc, int s, Spinor<float>& psi) {
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    CloverBlockF32 blk;
+    StageT<HALF>::clover_block(sc, s, b, blk);
+    cx<float> x[6], y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = psi.v[2 * b + i / 3][i % 3];
+    herm6_mul<float>(blk, x, y);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) psi.v[2 * b + i / 3][i % 3] = y[i];
+  }
+}
+
+__device__ __forceinline__ void st_store_x(float4* sx, int s, const Spinor<float>& a) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const cx<float> a0 = a.v[(2 * k) / 3][(2 * k) % 3];
+    const cx<float> a1 = a.v[(2 * k + 1) / 3][(2 * k + 1) % 3];
+    sx[k * 256 + s] = make_float4(a0.re, a0.im, a1.re, a1.im);
+  }
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using ST = StageT<HALF>;
+  float4* sx = reinterpret_cast<float4*>(smem);                              // 24 KB
+  unsigned char* sl = smem + 6 * 256 * 16;                                    // links
+  unsigned char* sc = sl + ST::LINK_BYTES;                                     // C_inv
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);
+  const Geom& g = a.g;
+  const int s = threadIdx.x;
+  const int dom = a.colour * g.nhalf + blockIdx.x;
+
+  if (s == 0) {
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, ST::LINK_BYTES + ST::CLOV_BYTES);
+    bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, bar);
+    bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, bar);
+  }
+  Spinor<float> src;
+  a.s_in.load(g, dom, s, src);
+  Spinor<float> acc;
+  zero(acc);
+  if (a.do_surface) {
+    st_inter<0, HALF>(g, a.x, a.links, dom, s, acc);
+    st_inter<1, HALF>(g, a.x, a.links, dom, s, acc);
+    st_inter<2, HALF>(g, a.x, a.links, dom, s, acc);
+    st_inter<3, HALF>(g, a.x, a.links, dom, s, acc);
+  }
+  __syncthreads();  // barrier initialisation visible to every thread
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    // a wait gave up: record it, give the copies one more bounded wait and
+    // leave (the decision is uniform across the CTA)
+    if (s == 0) atomicExch(a.status, QCD_ERR_TIMEOUT);
+    if (ok == false) mbar_wait_bounded(bar, 0);
+    return;
+  }
+  if (a.do_surface) {
+    st_clover<HALF>(sc, s, acc);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        src.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
+        src.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
+      }
+  }
+  st_store_x(sx, s, src);
+  __syncthreads();
+
+  Spinor<float> xk = src;
+  const int napp = a.n_jac + (a.do_update ? 1 : 0);
+  for (int it = 0; it < napp; ++it) {
+    zero(acc);
+    st_intra<0, HALF>(sx, sl, s, acc);
+    st_intra<1, HALF>(sx, sl, s, acc);
+    st_intra<2, HALF>(sx, sl, s, acc);
+    st_intra<3, HALF>(sx, sl, s, acc);
+    st_clover<HALF>(sc, s, acc);
+    if (it < a.n_jac) {
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          xk.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
+          xk.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
+        }
+      __syncthreads();
+      st_store_x(sx, s, xk);
+      __syncthreads();
+    } else {
+      Spinor<float> b;
+      a.b.load(g, dom, s, b);
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float re = src.v[sp][c].re + b.v[sp][c].re - xk.v[sp][c].re;
+          const float im = src.v[sp][c].im + b.v[sp][c].im - xk.v[sp][c].im;
+          acc.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, re);
+          acc.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, im);
+        }
+      a.s_out.store(g, dom, s, acc);
+    }
+  }
+  a.x.store(g, dom, s, xk);
+}
+
+// ---------------------------------------------------------------------------
+// staging layouts, built from the internal layouts
+// ---------------------------------------------------------------------------
+__global__ void build_link_stage_kernel(Geom g, const double2* u64, __half2* l16, float2* l32) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol * 4) return;
+  const int s = (int)(gid & 255);
+  const int mu = (int)((gid >> 8) & 3);
+  const int dom = (int)(gid >> 10);
+  for (int e = 0; e < 9; ++e) {
+    const double2 v = u64[(((size_t)((dom * 4 + mu) * 9 + e)) << 8) + s];
+    const size_t o = ((size_t)(dom * 4 + mu) * 256 + s) * 9 + e;
+    l16[o] = __floats2half2_rn((float)v.x, (float)v.y);
+    l32[o] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+__global__ void build_clover_stage_kernel(Geom g, const double2* c64, uint4* c16, float4* c32) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int s = (int)(gid & 255);
+  const int dom = (int)(gid >> 8);
+  __half2* h = reinterpret_cast<__half2*>(c16 + (size_t)(dom * 256 + s) * C16_U4);
+  float* f = reinterpret_cast<float*>(c32 + (size_t)(dom * 256 + s) * C32_F4);
+  for (int b = 0; b < 2; ++b) {
+    for (int k = 0; k < 18; ++k) {
+      const double2 v = c64[(((size_t)(dom * 36 + 18 * b + k)) << 8) + s];
+      h[20 * b + k] = __floats2half2_rn((float)v.x, (float)v.y);
+      f[36 * b + 2 * k] = (float)v.x;
+      f[36 * b + 2 * k + 1] = (float)v.y;
+    }
+    h[20 * b + 18] = __floats2half2_rn(0.f, 0.f);
+    h[20 * b + 19] = __floats2half2_rn(0.f, 0.f);
+  }
+  for (int k = 40; k < 44; ++k) h[k] = __floats2half2_rn(0.f, 0.f);
+  for (int k = 72; k < 76; ++k) f[k] = 0.f;
+}
+
+bool sap_staged_available(const qcd_ctx* ctx) {
+  const Geom& g = ctx->geom;
+  return g.d[0] == 4 && g.d[1] == 4 && g.d[2] == 4 && g.d[3] == 4 && ctx->st_link16 && ctx->st_clov16;
+}
+
+void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
+  const Geom& g = ctx->geom;
+  if (!(g.d[0] == 4 && g.d[1] == 4 && g.d[2] == 4 && g.d[3] == 4)) return;
+  const size_t nd = (size_t)g.ndom;
+  if (!ctx->st_link16) {
+    QCD_CUDA_CHECK(cudaMalloc(&ctx->st_link16, nd * StageT<true>::LINK_BYTES));
+    QCD_CUDA_CHECK(cudaMalloc(&ctx->st_link32, nd * StageT<false>::LINK_BYTES));
+    QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov16, nd * StageT<true>::CLOV_BYTES));
+    QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov32, nd * StageT<false>::CLOV_BYTES));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        6 * 256 * 16 + StageT<true>::LINK_BYTES + StageT<true>::CLOV_BYTES + 16));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        6 * 256 * 16 + StageT<false>::LINK_BYTES + StageT<false>::CLOV_BYTES + 16));
+  }
+  LaunchScope ls(ctx, QCD_KC_OTHER, st);
+  build_link_stage_kernel<<<grid_for(g.vol * 4, 256), 256, 0, st>>>(g, ctx->u64, (__half2*)ctx->st_link16,
+                                                                    (float2*)ctx->st_link32);
+  build_clover_stage_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g, ctx->cinv64,
+                                                                  (uint4*)ctx->st_clov16, (float4*)ctx->st_clov32);
+  check_launch();
+}
+
+template <bool HALF>
+static void staged_sequence(qcd_ctx* ctx, typename StageT<HALF>::SIO s_first_in, typename StageT<HALF>::SIO s,
+                            typename StageT<HALF>::SIO x, F32Spinor b, int n_sap, int n_jac, cudaStream_t st) {
+  StagedArgs<HALF> a;
+  a.g = ctx->geom;
+  a.n_jac = n_jac;
+  a.kappa = (float)ctx->kappa;
+  a.b = b;
+  a.x = x;
+  a.s_out = s;
+  a.links = (const unsigned char*)(HALF ? ctx->st_link16 : ctx->st_link32);
+  a.clov = (const unsigned char*)(HALF ? ctx->st_clov16 : ctx->st_clov32);
+  a.status = ctx->d_status;
+  const int smem = 6 * 256 * 16 + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 16;
+  for (int sweep = 0; sweep <= n_sap; ++sweep) {
+    a.s_in = sweep == 0 ? s_first_in : s;
+    a.do_update = sweep == n_sap ? 0 : 1;
+    for (int colour = 0; colour < 2; ++colour) {
+      a.colour = colour;
+      a.do_surface = (sweep == 0 && colour == 0) ? 0 : 1;
+      LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
+      sap_staged_kernel<HALF><<<ctx->geom.nhalf, ST_THREADS, smem, st>>>(a);
+      check_launch();
+    }
+  }
+}
+
+void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int n_sap,
+                             int n_jac, cudaStream_t st) {
+  staged_sequence<false>(ctx, s_first_in, s, x, b, n_sap, n_jac, st);
+}
+void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int n_sap,
+                             int n_jac, cudaStream_t st) {
+  staged_sequence<true>(ctx, s_first_in, s, x, b, n_sap, n_jac, st);
+}
+
+}  // namespace qcd
