@@ -722,7 +722,14 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     QCD_CUDA_CHECK(cudaMemcpyAsync(h_r2.data(), d_red + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaStreamSynchronize(st));
   };
-  residual();
+  if (P.x_is_guess) {
+    residual();
+  } else {
+    // x = 0: r = b exactly, no operator application needed
+    QCD_CUDA_CHECK(cudaMemcpyAsync(w->r64, w->b64, n2 * sizeof(double2) * nrhs, cudaMemcpyDeviceToDevice, st));
+    QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + nrhs, d_red, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, st));
+    QCD_CUDA_CHECK(cudaMemcpyAsync(h_r2.data(), d_red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  }
   QCD_CUDA_CHECK(cudaMemcpyAsync(h_b2.data(), d_red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   QCD_CUDA_CHECK(cudaStreamSynchronize(st));
 
