@@ -386,6 +386,8 @@ def main():
     e2e_s = (time.perf_counter() - te) / ne
     e2e_value = world / e2e_s
 
+    tuning = B.qcd_tuning_report(lat.ctx).strip().splitlines()
+
     # dominant kernel by device time in the timed region
     sap_n, sap_ms = prof[B.KC_SAP_BLOCK]
     total_ms = sum(v[1] for v in prof.values())
@@ -426,6 +428,7 @@ def main():
                               ((B.KC_DSLASH, "dslash_A"), (B.KC_SAP_BLOCK, "sap_block"), (B.KC_BLAS, "blas"),
                                (B.KC_DOUBLE, "float64"), (B.KC_OTHER, "other"))},
         "clocks": clk,
+        "tuning": tuning,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(b_host.numel() * 8),
                 "d2h_bytes_per_step": int(x_host.numel() * 8)},

@@ -239,6 +239,17 @@ int qcd_profile_enable(qcd_ctx* ctx, int enable);
  * (synchronises the events).  reset = 1 clears the counters afterwards. */
 int qcd_profile_read(qcd_ctx* ctx, int kernel_class, long long* launches, double* ms, int reset);
 
+/* Launch-shape autotuning (on by default).  With tuning on, the first call of
+ * a tunable kernel (the float32 D / D^dag / A operator) for a given number
+ * of right-hand sides times each compiled launch shape (threads per block,
+ * blocks per SM) on the real arguments and keeps the fastest; the shapes
+ * change scheduling only, not the arithmetic.  enable = 0 turns tuning off
+ * and forgets the choices (the default shape is then used). */
+int qcd_set_tuning(qcd_ctx* ctx, int enable);
+
+/* Text report of the tuned choices, one line per key: "<key> <shape> <ms>". */
+int qcd_tuning_report(qcd_ctx* ctx, char* buf, size_t len);
+
 /* Number of kernels the library has launched on this context so far. */
 int qcd_launch_count(const qcd_ctx* ctx, long long* count);
 

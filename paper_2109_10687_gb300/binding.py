@@ -79,6 +79,8 @@ _SIGS = {
     "qcd_profile_enable": (_I, [_P, _I]),
     "qcd_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), _I]),
     "qcd_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "qcd_set_tuning": (_I, [_P, _I]),
+    "qcd_tuning_report": (_I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 
@@ -260,3 +262,13 @@ def qcd_launch_count(ctx):
     n = ctypes.c_longlong()
     check(ctx, lib().qcd_launch_count(ctx, ctypes.byref(n)))
     return n.value
+
+
+def qcd_set_tuning(ctx, enable=True):
+    return check(ctx, lib().qcd_set_tuning(ctx, int(bool(enable))))
+
+
+def qcd_tuning_report(ctx):
+    buf = ctypes.create_string_buffer(4096)
+    check(ctx, lib().qcd_tuning_report(ctx, buf, len(buf)))
+    return buf.value.decode()

@@ -355,6 +355,7 @@ extern "C" int qcd_create(const int dims[4], const int domain[4], int bc_t, int 
 extern "C" int qcd_destroy(qcd_ctx* ctx) {
   if (!ctx) return QCD_OK;
   workspace_free(ctx);
+  tuner_free(ctx);
   void* ptrs[] = {ctx->d_nbr, ctx->d_lex2dom, ctx->d_tflag, ctx->u64, ctx->u32, ctx->u16, ctx->clov64,
                   ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status,
                   ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32};

@@ -7,6 +7,8 @@
 // rebuilt into the accumulator: 168 flop per hop, 1320 for the hopping term,
 // plus the clover block multiply.
 
+#include <cstdio>
+
 #include "qcd_internal.cuh"
 
 namespace qcd {
@@ -81,17 +83,24 @@ __device__ __forceinline__ void hopping(const Geom& g, const SIO& in, const LP& 
 // D:    out = (1 + C) x - kappa H x
 // D^dag: out = (1 + C) x - kappa H^dag x   (gamma_5 H gamma_5 swaps the projectors)
 // A:    out = x - kappa C_inv H x
-template <typename R, int MODE>
-__global__ void __launch_bounds__(128) dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in,
-                                                     typename Prec<R>::LP U, typename Prec<R>::CP clov, R kappa) {
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+//
+// Launch shape: THREADS per block, at least MINB blocks per SM (a register
+// budget); the autotuner picks among the instantiated shapes.  Blocks are
+// numbered rhs-fastest, so the nrhs blocks that share a tile of sites (and
+// its links and clover) run back to back and reuse them from L2.
+template <typename R, int MODE, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+    dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in, typename Prec<R>::LP U,
+                  typename Prec<R>::CP clov, R kappa, int nrhs) {
+  const int rhs = blockIdx.x % nrhs;
+  const long long gid = (blockIdx.x / nrhs) * (long long)THREADS + threadIdx.x;
   if (gid >= g.vol) return;
   // domains are visited in lexicographic order, so that the neighbouring
   // domains whose surface spinors a domain reads are processed at about the
   // same time and their data is still in L2
   const int dom = __ldg(g.lex2dom + (int)(gid >> g.logvd));
   const int s = (int)(gid & (g.vd - 1));
-  const int rhs_off = blockIdx.y * g.ndom;
+  const int rhs_off = rhs * g.ndom;
   Spinor<R> acc;
   if (MODE == MODE_DDAG) hopping<+1, -1, 0>(g, in, U, dom, s, rhs_off, acc);
   else hopping<-1, +1, 0>(g, in, U, dom, s, rhs_off, acc);
@@ -153,33 +162,54 @@ __global__ void __launch_bounds__(128) ablock_kernel(Geom g, F32Spinor out, F32S
   out.store(g, dom, s, res);
 }
 
+template <typename R, int MODE, int THREADS, int MINB>
+static void launch_dslash_shape(const Geom& g, void* out, const void* in, const void* U, const void* clov, R kappa,
+                                int nrhs, cudaStream_t st) {
+  using P = Prec<R>;
+  const long long blocks = (long long)grid_for(g.vol, THREADS) * nrhs;
+  QCD_REQUIRE(blocks < (1LL << 31), QCD_ERR_ARG, "lattice too large for one launch");
+  dslash_kernel<R, MODE, THREADS, MINB><<<(unsigned)blocks, THREADS, 0, st>>>(
+      g, typename P::SIO{(decltype(P::SIO::p))out}, typename P::SIO{(decltype(P::SIO::p))in},
+      typename P::LP{(decltype(P::LP::p))U}, typename P::CP{(decltype(P::CP::p))clov}, kappa, nrhs);
+}
+
+// float32 launch shapes the autotuner chooses from
+template <int MODE>
+static void launch_dslash_f32(int variant, const Geom& g, void* out, const void* in, const void* U, const void* clov,
+                              float kappa, int nrhs, cudaStream_t st) {
+  switch (variant) {
+    case 0: launch_dslash_shape<float, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 1: launch_dslash_shape<float, MODE, 128, 5>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 2: launch_dslash_shape<float, MODE, 128, 6>(g, out, in, U, clov, kappa, nrhs, st); break;
+    default: launch_dslash_shape<float, MODE, 256, 2>(g, out, in, U, clov, kappa, nrhs, st); break;
+  }
+}
+static const char* kDslashShapes[] = {"128x4", "128x5", "128x6", "256x2"};
+
 void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st) {
   const Geom& g = ctx->geom;
-  const int block = 128;
-  dim3 grid(grid_for(g.vol, block), nrhs);
   if (prec == QCD_PREC_DOUBLE) {
     QCD_REQUIRE(mode != MODE_A, QCD_ERR_ARG, "A is provided in float32 only");
     LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-    F64Spinor o{(double2*)out}, i{(double2*)in};
-    LinkPtr<double> U{ctx->u64};
-    CloverPtrF64 c{ctx->clov64};
-    if (mode == MODE_D) dslash_kernel<double, MODE_D><<<grid, block, 0, st>>>(g, o, i, U, c, ctx->kappa);
-    else dslash_kernel<double, MODE_DDAG><<<grid, block, 0, st>>>(g, o, i, U, c, ctx->kappa);
+    if (mode == MODE_D)
+      launch_dslash_shape<double, MODE_D, 128, 1>(g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
+    else
+      launch_dslash_shape<double, MODE_DDAG, 128, 1>(g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
     check_launch();
   } else if (prec == QCD_PREC_SINGLE) {
-    LaunchScope ls(ctx, QCD_KC_DSLASH, st);
-    F32Spinor o{(float4*)out}, i{(float4*)in};
-    LinkPtr<float> U{ctx->u32};
     const float k = (float)ctx->kappa;
-    if (mode == MODE_A) {
-      CloverPtrF32 c{ctx->cinv32};
-      dslash_kernel<float, MODE_A><<<grid, block, 0, st>>>(g, o, i, U, c, k);
-    } else {
-      CloverPtrF32 c{ctx->clov32};
-      if (mode == MODE_D) dslash_kernel<float, MODE_D><<<grid, block, 0, st>>>(g, o, i, U, c, k);
-      else dslash_kernel<float, MODE_DDAG><<<grid, block, 0, st>>>(g, o, i, U, c, k);
-    }
-    check_launch();
+    const void* clov = mode == MODE_A ? (const void*)ctx->cinv32 : (const void*)ctx->clov32;
+    auto run = [&](int v) {
+      if (mode == MODE_A) launch_dslash_f32<MODE_A>(v, g, out, in, ctx->u32, clov, k, nrhs, st);
+      else if (mode == MODE_D) launch_dslash_f32<MODE_D>(v, g, out, in, ctx->u32, clov, k, nrhs, st);
+      else launch_dslash_f32<MODE_DDAG>(v, g, out, in, ctx->u32, clov, k, nrhs, st);
+      check_launch();
+    };
+    char key[64];
+    std::snprintf(key, sizeof key, "dslash_f32_mode%d_nrhs%d", mode, nrhs);
+    const int v = tune_pick(ctx, key, 4, kDslashShapes, run, st);
+    LaunchScope ls(ctx, QCD_KC_DSLASH, st);
+    run(v);
   } else {
     throw Error{QCD_ERR_ARG, "operator precision must be DOUBLE or SINGLE"};
   }

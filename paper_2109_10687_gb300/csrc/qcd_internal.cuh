@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 
 #include "qcd_gb300.h"
@@ -501,6 +502,7 @@ __device__ __forceinline__ void clover_mul(const Ptr& cp, const Geom& g, int dom
 // ---------------------------------------------------------------------------
 struct Workspace;
 struct Profiler;
+struct Tuner;
 
 }  // namespace qcd
 
@@ -532,6 +534,7 @@ struct qcd_ctx {
   bool force_generic_sap = false;  // testing: use the generic SAP kernel
   qcd::Workspace* ws = nullptr;
   qcd::Profiler* prof = nullptr;
+  qcd::Tuner* tuner = nullptr;
   long long launches = 0;
   std::string err;
 };
@@ -583,6 +586,14 @@ inline size_t spinor_bytes(const Geom& g, int prec) {
 
 inline int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
 
+// Autotuner: returns the launch variant to use for `key`.  The first call per
+// key with tuning on (and outside stream capture) times every variant with
+// CUDA events -- run(v) must be an out-of-place launch whose repetition is
+// harmless -- and remembers the fastest; later calls return it.
+int tune_pick(qcd_ctx* ctx, const char* key, int nvariants, const char* const* names,
+              const std::function<void(int)>& run, cudaStream_t st);
+void tuner_free(qcd_ctx* ctx);
+
 // internal entry points implemented in the other translation units
 void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st);
 void clover_apply_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int inverse, int nrhs,
@@ -591,10 +602,12 @@ void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col
 void build_clover_launch(qcd_ctx* ctx, cudaStream_t st);
 void build_sap_staging(qcd_ctx* ctx, cudaStream_t st);
 bool sap_staged_available(const qcd_ctx* ctx);
-void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int n_sap,
-                             int n_jac, cudaStream_t st);
-void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int n_sap,
-                             int n_jac, cudaStream_t st);
+void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
+                             int n_sap, int n_jac, cudaStream_t st);
+void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int nrhs,
+                             int n_sap, int n_jac, cudaStream_t st);
+void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
+                      void* ws_s, void* ws_x16, void* ws_b16, cudaStream_t st);
 void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
 
 // dslash modes

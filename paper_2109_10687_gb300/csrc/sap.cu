@@ -206,11 +206,12 @@ __global__ void __launch_bounds__(SAP_THREADS) sap_block_kernel(SapArgs<SIO, LP,
   if (active) a.x.store(g, dom, s, xk);
 }
 
-// float32 <-> float16 field conversion (internal layouts, same site order)
+// float32 <-> float16 field conversion (internal layouts, same site order;
+// blockIdx.y selects the right-hand side)
 __global__ void f32_to_f16_kernel(Geom g, F16Spinor out, F32Spinor in) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= g.vol) return;
-  const int dom = (int)(gid >> g.logvd), s = (int)(gid & (g.vd - 1));
+  const int dom = (int)(gid >> g.logvd) + blockIdx.y * g.ndom, s = (int)(gid & (g.vd - 1));
   Spinor<float> a;
   in.load(g, dom, s, a);
   out.store(g, dom, s, a);
@@ -218,7 +219,7 @@ __global__ void f32_to_f16_kernel(Geom g, F16Spinor out, F32Spinor in) {
 __global__ void f16_to_f32_kernel(Geom g, F32Spinor out, F16Spinor in) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= g.vol) return;
-  const int dom = (int)(gid >> g.logvd), s = (int)(gid & (g.vd - 1));
+  const int dom = (int)(gid >> g.logvd) + blockIdx.y * g.ndom, s = (int)(gid & (g.vd - 1));
   Spinor<float> a;
   in.load(g, dom, s, a);
   out.store(g, dom, s, a);
@@ -260,40 +261,56 @@ static void sap_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spinor b
   }
 }
 
-// x = M_SAP b on float32 fields; ws_s: float32 (or float16) workspace for s,
-// ws_x16 / ws_b16: float16 workspaces (sap_prec == HALF only).
-void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int n_sap, int n_jac, int sap_prec, void* ws_s,
-                      void* ws_x16, void* ws_b16, cudaStream_t st) {
+// x = M_SAP b for nrhs stacked float32 fields.  ws_s holds s (float32 or
+// float16), ws_x16 / ws_b16 the float16 x and source (sap_prec == HALF); all
+// three are sized for nrhs right-hand sides.  With the shared-memory kernel
+// all right-hand sides go through each launch and share its staged links and
+// C_inv; the generic kernel runs them one after the other.
+void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
+                      void* ws_s, void* ws_x16, void* ws_b16, cudaStream_t st) {
   const Geom& g = ctx->geom;
   const bool staged = sap_staged_available(ctx) && !ctx->force_generic_sap;
+  const size_t v = (size_t)g.vol;
+  const size_t v4 = v * 6;
   if (sap_prec == QCD_PREC_SINGLE) {
-    F32Spinor xs{x}, bs{(float4*)b}, ss{(float4*)ws_s};
-    if (staged)
-      sap_staged_sequence_f32(ctx, bs, ss, xs, bs, n_sap, n_jac, st);
-    else
-      sap_sequence<F32Spinor, LinkPtr<float>, CloverPtrF32, CloverBlockF32>(
-          ctx, bs, ss, xs, bs, LinkPtr<float>{ctx->u32}, CloverPtrF32{ctx->cinv32}, n_sap, n_jac, st);
+    if (staged) {
+      F32Spinor xs{x}, bs{(float4*)b}, ss{(float4*)ws_s};
+      sap_staged_sequence_f32(ctx, bs, ss, xs, bs, nrhs, n_sap, n_jac, st);
+    } else {
+      for (int r = 0; r < nrhs; ++r) {
+        F32Spinor xs{x + r * v4}, bs{(float4*)b + r * v4}, ss{(float4*)ws_s + r * v4};
+        sap_sequence<F32Spinor, LinkPtr<float>, CloverPtrF32, CloverBlockF32>(
+            ctx, bs, ss, xs, bs, LinkPtr<float>{ctx->u32}, CloverPtrF32{ctx->cinv32}, n_sap, n_jac, st);
+      }
+    }
+    return;
+  }
+  const size_t nv = v * nrhs;
+  F16Spinor s16{(uint4*)ws_s, (float*)((uint4*)ws_s + 3 * nv)};
+  F16Spinor x16{(uint4*)ws_x16, (float*)((uint4*)ws_x16 + 3 * nv)};
+  F16Spinor b16{(uint4*)ws_b16, (float*)((uint4*)ws_b16 + 3 * nv)};
+  const dim3 cgrid(grid_for(g.vol, 256), nrhs);
+  {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    f32_to_f16_kernel<<<cgrid, 256, 0, st>>>(g, b16, F32Spinor{(float4*)b});
+    check_launch();
+  }
+  if (staged) {
+    sap_staged_sequence_f16(ctx, b16, s16, x16, F32Spinor{(float4*)b}, nrhs, n_sap, n_jac, st);
   } else {
-    const size_t v = (size_t)g.vol;
-    F16Spinor s16{(uint4*)ws_s, (float*)((uint4*)ws_s + 3 * v)};
-    F16Spinor x16{(uint4*)ws_x16, (float*)((uint4*)ws_x16 + 3 * v)};
-    F16Spinor b16{(uint4*)ws_b16, (float*)((uint4*)ws_b16 + 3 * v)};
-    {
-      LaunchScope ls(ctx, QCD_KC_BLAS, st);
-      f32_to_f16_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g, b16, F32Spinor{(float4*)b});
-      check_launch();
-    }
-    if (staged)
-      sap_staged_sequence_f16(ctx, b16, s16, x16, F32Spinor{(float4*)b}, n_sap, n_jac, st);
-    else
+    for (int r = 0; r < nrhs; ++r) {
+      F16Spinor sr{s16.p + 3 * v * r, s16.nrm + v * r};
+      F16Spinor xr{x16.p + 3 * v * r, x16.nrm + v * r};
+      F16Spinor br{b16.p + 3 * v * r, b16.nrm + v * r};
       sap_sequence<F16Spinor, LinkPtrHalf, CloverPtrF16, CloverBlockF32>(
-          ctx, b16, s16, x16, F32Spinor{(float4*)b}, LinkPtrHalf{ctx->u16}, CloverPtrF16{ctx->cinv16}, n_sap, n_jac,
-          st);
-    {
-      LaunchScope ls(ctx, QCD_KC_BLAS, st);
-      f16_to_f32_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g, F32Spinor{x}, x16);
-      check_launch();
+          ctx, br, sr, xr, F32Spinor{(float4*)b + r * v4}, LinkPtrHalf{ctx->u16}, CloverPtrF16{ctx->cinv16}, n_sap,
+          n_jac, st);
     }
+  }
+  {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    f16_to_f32_kernel<<<cgrid, 256, 0, st>>>(g, F32Spinor{x}, x16);
+    check_launch();
   }
 }
 

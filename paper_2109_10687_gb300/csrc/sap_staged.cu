@@ -88,7 +88,7 @@ struct StageT<false> {
 template <bool HALF>
 struct StagedArgs {
   Geom g;
-  int colour, n_jac, do_surface, do_update;
+  int colour, n_jac, do_surface, do_update, nrhs;
   float kappa;
   typename StageT<HALF>::SIO s_in, s_out, x;
   F32Spinor b;
@@ -181,7 +181,7 @@ __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* 
 // acc += both domain-leaving hops of direction MU (operand x and links from memory)
 template <int MU, bool HALF, typename SIO>
 __device__ __forceinline__ void st_inter(const Geom& g, const SIO& x, const unsigned char* links, int dom, int s,
-                                         Spinor<float>& acc) {
+                                         int rhs_off, Spinor<float>& acc) {
   constexpr int step = 1 << (2 * MU);
   const int c = lc<MU>(s);
   constexpr size_t dom_bytes = StageT<HALF>::LINK_BYTES;
@@ -189,7 +189,7 @@ __device__ __forceinline__ void st_inter(const Geom& g, const SIO& x, const unsi
     const int nd = __ldg(g.nbr + dom * 8 + 2 * MU);
     const int sign = ((__ldg(g.tflag + dom) >> (2 * MU)) & 1) ? g.bc_t : 1;
     Spinor<float> p;
-    x.load(g, nd, s - 3 * step, p);
+    x.load(g, nd + rhs_off, s - 3 * step, p);
     HalfSpinor<float> h, uh;
     project<MU, -1>(p, h);
     const SU3<float> u = StageT<HALF>::link(links + dom * dom_bytes, MU, s);
@@ -202,7 +202,7 @@ __device__ __forceinline__ void st_inter(const Geom& g, const SIO& x, const unsi
     const int sign = ((__ldg(g.tflag + dom) >> (2 * MU + 1)) & 1) ? g.bc_t : 1;
     const int ns = s + 3 * step;
     Spinor<float> p;
-    x.load(g, nd, ns, p);
+    x.load(g, nd + rhs_off, ns, p);
     HalfSpinor<float> h, uh;
     project<MU, +1>(p, h);
     const SU3<float> u = StageT<HALF>::link(links + nd * dom_bytes, MU, ns);
@@ -254,74 +254,82 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
     bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, bar);
     bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, bar);
   }
-  Spinor<float> src;
-  a.s_in.load(g, dom, s, src);
-  Spinor<float> acc;
-  zero(acc);
-  if (a.do_surface) {
-    st_inter<0, HALF>(g, a.x, a.links, dom, s, acc);
-    st_inter<1, HALF>(g, a.x, a.links, dom, s, acc);
-    st_inter<2, HALF>(g, a.x, a.links, dom, s, acc);
-    st_inter<3, HALF>(g, a.x, a.links, dom, s, acc);
-  }
-  __syncthreads();  // barrier initialisation visible to every thread
-  const bool ok = mbar_wait_bounded(bar, 0);
-  if (__syncthreads_or(!ok)) {
-    // a wait gave up: record it, give the copies one more bounded wait and
-    // leave (the decision is uniform across the CTA)
-    if (s == 0) atomicExch(a.status, QCD_ERR_TIMEOUT);
-    if (ok == false) mbar_wait_bounded(bar, 0);
-    return;
-  }
-  if (a.do_surface) {
-    st_clover<HALF>(sc, s, acc);
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        src.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
-        src.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
-      }
-  }
-  st_store_x(sx, s, src);
-  __syncthreads();
-
-  Spinor<float> xk = src;
-  const int napp = a.n_jac + (a.do_update ? 1 : 0);
-  for (int it = 0; it < napp; ++it) {
+  for (int r = 0; r < a.nrhs; ++r) {
+    const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
+    const int rhs_off = r * g.ndom;
+    Spinor<float> src;
+    a.s_in.load(g, domr, s, src);
+    Spinor<float> acc;
     zero(acc);
-    st_intra<0, HALF>(sx, sl, s, acc);
-    st_intra<1, HALF>(sx, sl, s, acc);
-    st_intra<2, HALF>(sx, sl, s, acc);
-    st_intra<3, HALF>(sx, sl, s, acc);
-    st_clover<HALF>(sc, s, acc);
-    if (it < a.n_jac) {
-#pragma unroll
-      for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          xk.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
-          xk.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
-        }
-      __syncthreads();
-      st_store_x(sx, s, xk);
-      __syncthreads();
-    } else {
-      Spinor<float> b;
-      a.b.load(g, dom, s, b);
-#pragma unroll
-      for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float re = src.v[sp][c].re + b.v[sp][c].re - xk.v[sp][c].re;
-          const float im = src.v[sp][c].im + b.v[sp][c].im - xk.v[sp][c].im;
-          acc.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, re);
-          acc.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, im);
-        }
-      a.s_out.store(g, dom, s, acc);
+    if (a.do_surface) {
+      st_inter<0, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
+      st_inter<1, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
+      st_inter<2, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
+      st_inter<3, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
     }
+    if (r == 0) {
+      __syncthreads();  // barrier initialisation visible to every thread
+      const bool ok = mbar_wait_bounded(bar, 0);
+      if (__syncthreads_or(!ok)) {
+        // a wait gave up: record it, give the copies one more bounded wait and
+        // leave (the decision is uniform across the CTA)
+        if (s == 0) atomicExch(a.status, QCD_ERR_TIMEOUT);
+        if (!ok) mbar_wait_bounded(bar, 0);
+        return;
+      }
+    } else {
+      __syncthreads();  // every thread is done with the previous rhs's x in shared memory
+    }
+    if (a.do_surface) {
+      st_clover<HALF>(sc, s, acc);
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          src.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
+          src.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
+        }
+    }
+    st_store_x(sx, s, src);
+    __syncthreads();
+
+    Spinor<float> xk = src;
+    const int napp = a.n_jac + (a.do_update ? 1 : 0);
+    for (int it = 0; it < napp; ++it) {
+      zero(acc);
+      st_intra<0, HALF>(sx, sl, s, acc);
+      st_intra<1, HALF>(sx, sl, s, acc);
+      st_intra<2, HALF>(sx, sl, s, acc);
+      st_intra<3, HALF>(sx, sl, s, acc);
+      st_clover<HALF>(sc, s, acc);
+      if (it < a.n_jac) {
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            xk.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
+            xk.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
+          }
+        __syncthreads();
+        st_store_x(sx, s, xk);
+        __syncthreads();
+      } else {
+        Spinor<float> b;
+        a.b.load(g, domr, s, b);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float re = src.v[sp][c].re + b.v[sp][c].re - xk.v[sp][c].re;
+            const float im = src.v[sp][c].im + b.v[sp][c].im - xk.v[sp][c].im;
+            acc.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, re);
+            acc.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, im);
+          }
+        a.s_out.store(g, domr, s, acc);
+      }
+    }
+    a.x.store(g, domr, s, xk);
   }
-  a.x.store(g, dom, s, xk);
 }
 
 // ---------------------------------------------------------------------------
@@ -391,9 +399,11 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
 
 template <bool HALF>
 static void staged_sequence(qcd_ctx* ctx, typename StageT<HALF>::SIO s_first_in, typename StageT<HALF>::SIO s,
-                            typename StageT<HALF>::SIO x, F32Spinor b, int n_sap, int n_jac, cudaStream_t st) {
+                            typename StageT<HALF>::SIO x, F32Spinor b, int nrhs, int n_sap, int n_jac,
+                            cudaStream_t st) {
   StagedArgs<HALF> a;
   a.g = ctx->geom;
+  a.nrhs = nrhs;
   a.n_jac = n_jac;
   a.kappa = (float)ctx->kappa;
   a.b = b;
@@ -416,13 +426,13 @@ static void staged_sequence(qcd_ctx* ctx, typename StageT<HALF>::SIO s_first_in,
   }
 }
 
-void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int n_sap,
-                             int n_jac, cudaStream_t st) {
-  staged_sequence<false>(ctx, s_first_in, s, x, b, n_sap, n_jac, st);
+void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
+                             int n_sap, int n_jac, cudaStream_t st) {
+  staged_sequence<false>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
 }
-void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int n_sap,
-                             int n_jac, cudaStream_t st) {
-  staged_sequence<true>(ctx, s_first_in, s, x, b, n_sap, n_jac, st);
+void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int nrhs,
+                             int n_sap, int n_jac, cudaStream_t st) {
+  staged_sequence<true>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
 }
 
 }  // namespace qcd

@@ -26,8 +26,6 @@
 
 namespace qcd {
 
-void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int n_sap, int n_jac, int sap_prec, void* ws_s,
-                      void* ws_x16, void* ws_b16, cudaStream_t st);
 
 struct Scal {
   double rho0_re, rho0_im;
@@ -108,9 +106,9 @@ static Workspace* workspace(qcd_ctx* ctx, int nrhs, bool solver) {
     const size_t b64 = (size_t)g.vol * 12 * sizeof(double2) * keep_nrhs;
     double2** v64[] = {&w->x64, &w->r64, &w->b64, &w->t64};
     for (auto v : v64) QCD_CUDA_CHECK(cudaMalloc(v, b64));
-    QCD_CUDA_CHECK(cudaMalloc(&w->sap_s, spinor_bytes(g, QCD_PREC_SINGLE)));
-    QCD_CUDA_CHECK(cudaMalloc(&w->sap_x16, spinor_bytes(g, QCD_PREC_HALF)));
-    QCD_CUDA_CHECK(cudaMalloc(&w->sap_b16, spinor_bytes(g, QCD_PREC_HALF)));
+    QCD_CUDA_CHECK(cudaMalloc(&w->sap_s, spinor_bytes(g, QCD_PREC_SINGLE) * keep_nrhs));
+    QCD_CUDA_CHECK(cudaMalloc(&w->sap_x16, spinor_bytes(g, QCD_PREC_HALF) * keep_nrhs));
+    QCD_CUDA_CHECK(cudaMalloc(&w->sap_b16, spinor_bytes(g, QCD_PREC_HALF) * keep_nrhs));
   }
   return w;
 }
@@ -470,8 +468,7 @@ struct Launcher {
 
 static void am_sap(qcd_ctx* ctx, Workspace* w, float4* z, float4* out, const float4* in, int nrhs, int n_sap, int n_jac,
                    int sap_prec, cudaStream_t st) {
-  for (int r = 0; r < nrhs; ++r)
-    sap_apply_launch(ctx, z + r * w->v4, in + r * w->v4, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16, w->sap_b16, st);
+  sap_apply_launch(ctx, z, in, nrhs, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16, w->sap_b16, st);
   dslash_launch(ctx, out, z, QCD_PREC_SINGLE, MODE_A, nrhs, st);
 }
 
@@ -618,8 +615,8 @@ extern "C" int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap,
   if (with_A) {
     am_sap(ctx, w, w->tmp32, (float4*)out, (const float4*)in, 1, n_sap, n_jac, sap_prec, st);
   } else {
-    sap_apply_launch(ctx, (float4*)out, (const float4*)in, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16, w->sap_b16,
-                     st);
+    sap_apply_launch(ctx, (float4*)out, (const float4*)in, 1, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16,
+                     w->sap_b16, st);
   }
   API_END(ctx)
 }
