@@ -18,6 +18,7 @@ Canonical layout (the one the paper quotes for the K computer, Sec. 4):
 from .fields import (  # noqa: F401
     gellmann_matrices,
     random_su3_field,
+    random_su3_field_fast,
     random_su3_sites,
     gaussian_spinor,
     point_source,

@@ -67,6 +67,28 @@ def random_su3_field(dims, eps, seed):
     return u
 
 
+def random_su3_field_fast(dims, eps, seed, device="cuda", chunk=1 << 21):
+    """Same draws as ``random_su3_field``; the exponential exp(i eps H) is taken
+    on ``device`` with torch's batched Hermitian eigendecomposition (float64),
+    in chunks of ``chunk`` links, which makes 48^4 and 64^4 fields practical.
+    Returns a numpy complex128 array in the canonical layout."""
+    import torch
+
+    shape = lattice_shape(dims)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    coef = rng.standard_normal(shape + (4, 8)).reshape(-1, 8)
+    lam = torch.from_numpy(gellmann_matrices() / 2).to(device)
+    out = np.empty((coef.shape[0], 3, 3), dtype=np.complex128)
+    for a in range(0, coef.shape[0], chunk):
+        c = torch.from_numpy(coef[a:a + chunk]).to(device=device, dtype=torch.complex128)
+        h = torch.einsum("na,aij->nij", c, lam)
+        w, v = torch.linalg.eigh(h)
+        ph = torch.exp(1j * float(eps) * w.to(torch.complex128))
+        u = torch.einsum("nij,nj,nkj->nik", v, ph, v.conj())
+        out[a:a + chunk] = u.cpu().numpy()
+    return out.reshape(shape + (4, 3, 3))
+
+
 def random_su3_sites(dims, seed, eps=3.0):
     """One SU(3) matrix per site, ``[t][z][y][x][3][3]`` (a gauge transformation)."""
     shape = lattice_shape(dims)

@@ -215,3 +215,11 @@ def test_pointwise_matches_whole_lattice():
             c = tuple(int(rng.integers(0, dims[mu])) for mu in range(4))
             got = pointwise.D_at(u, x, c, 0.13, 1.2, g, -1)
             assert np.allclose(got, full[c[3], c[2], c[1], c[0]], atol=1e-12)
+
+
+def test_fast_generator_matches_reference_generator():
+    """The torch-exponentiated generator draws the same links as the numpy one."""
+    from lattice_inputs import random_su3_field_fast
+    a = random_su3_field((4, 4, 4, 8), 0.3, 7)
+    b = random_su3_field_fast((4, 4, 4, 8), 0.3, 7, device="cpu", chunk=1000)
+    assert np.abs(a - b).max() < 1e-13
