@@ -183,6 +183,24 @@ int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac,
  * across blocks in float64, in a fixed order (deterministic). */
 int qcd_norm2(qcd_ctx* ctx, double* result, const void* a, int prec, int nrhs, void* stream);
 
+/* |a|^2 like qcd_norm2, for callers that must not allocate device memory
+ * during the call -- for example code running under a caching allocator or
+ * memory pool that owns all free device memory, or code that must not
+ * trigger the implicit device synchronisation a cudaMalloc can cause.  The
+ * paper has no counterpart; this is an interface convenience.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Its scratch (per-block partial sums, completion counters and
+ * results) is a static device array of about 514 KB inside the library,
+ * held by every GPU that loads the library until the process exits.  Limits:
+ * 1 <= nrhs <= 16 (QCD_ERR_ARG otherwise).  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * result: host pointer, nrhs doubles; a: internal-layout field of precision
+ * SINGLE or DOUBLE.  Synchronises the stream. */
+int qcd_norm2_noalloc(qcd_ctx* ctx, double* result, const void* a, int prec, int nrhs, void* stream);
+
 /* result[0] + i result[1] = <a|b> = a^dag b (host pointer). */
 int qcd_cdot(qcd_ctx* ctx, double result[2], const void* a, const void* b, int prec, int nrhs,
              void* stream);

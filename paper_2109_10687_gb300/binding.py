@@ -72,6 +72,7 @@ _SIGS = {
     "qcd_apply_A_block": (_I, [_P, _P, _P, _I, _I, _P]),
     "qcd_sap_apply": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
     "qcd_norm2": (_I, [_P, ctypes.POINTER(_D), _P, _I, _I, _P]),
+    "qcd_norm2_noalloc": (_I, [_P, ctypes.POINTER(_D), _P, _I, _I, _P]),
     "qcd_cdot": (_I, [_P, ctypes.POINTER(_D), _P, _P, _I, _I, _P]),
     "qcd_solve": (_I, [_P, _P, _P, _I, _I, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P]),
     "qcd_solve_params_default": (_I, [ctypes.POINTER(SolveParams)]),
@@ -214,6 +215,13 @@ def qcd_sap_apply(ctx, out, inp, n_sap, n_jac, sap_prec=PREC_SINGLE, with_A=0, s
 def qcd_norm2(ctx, a, prec=PREC_SINGLE, nrhs=1, stream=None):
     out = (ctypes.c_double * nrhs)()
     check(ctx, lib().qcd_norm2(ctx, out, _ptr(a), int(prec), int(nrhs), _stream(stream)))
+    return list(out)
+
+
+def qcd_norm2_noalloc(ctx, a, prec=PREC_SINGLE, nrhs=1, stream=None):
+    """|a|^2 through the entry point that allocates no device memory."""
+    out = (ctypes.c_double * nrhs)()
+    check(ctx, lib().qcd_norm2_noalloc(ctx, out, _ptr(a), int(prec), int(nrhs), _stream(stream)))
     return list(out)
 
 

@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "qcd_internal.cuh"
@@ -198,10 +199,11 @@ __device__ __forceinline__ float norm4(float4 a) { return a.x * a.x + a.y * a.y 
   unsigned* cnt = counters + rhs;
 
 // |a|^2 -> out[rhs]
-__global__ void k_norm2(const float4* __restrict__ a, size_t n4, double* out, double* partials, unsigned* counters,
-                        Scal* scal) {
-  RHS_SETUP
-  (void)sc;
+__global__ void k_norm2(const float4* __restrict__ a, size_t n4, double* out, double* partials, unsigned* counters) {
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n4;
+  double* part = partials + (size_t)rhs * MAX_RED_OUT * gridDim.x;
+  unsigned* cnt = counters + rhs;
   float s = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
     s += norm4(a[off + i]);
@@ -565,6 +567,42 @@ static int bicgstab_sap(qcd_ctx* ctx, Workspace* w, const float4* b32, int nrhs,
   return it;
 }
 
+// ---------------------------------------------------------------------------
+// |a|^2 without any allocation (qcd_norm2_noalloc)
+// ---------------------------------------------------------------------------
+// Scratch of the reduction (per-block partial sums, completion counters and
+// the results) in a file-scope device array instead of the context's
+// workspace.  Every GPU that loads the library holds it (about 514 KB) until
+// the process exits; all calls share it.
+constexpr int NOALLOC_MAX_RHS = 16;
+constexpr int NOALLOC_MAX_BLOCKS = 1024;
+struct NoAllocScratch {
+  double partials[MAX_RED_OUT * NOALLOC_MAX_BLOCKS * NOALLOC_MAX_RHS];
+  double result[NOALLOC_MAX_RHS];
+  unsigned counters[NOALLOC_MAX_RHS];
+};
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol itself is only a host-side stand-in, never a device address; the
+// address is looked up once per device with that device current.
+static NoAllocScratch* noalloc_scratch_address() {
+  static std::mutex mu;
+  static NoAllocScratch* addr[256] = {nullptr};
+  int dev = 0;
+  QCD_CUDA_CHECK(cudaGetDevice(&dev));
+  QCD_REQUIRE(dev >= 0 && dev < 256, QCD_ERR_ARG, "qcd_norm2_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      throw Error{QCD_ERR_CUDA, std::string("qcd_norm2_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e)};
+    addr[dev] = static_cast<NoAllocScratch*>(p);
+  }
+  return addr[dev];
+}
+
 }  // namespace qcd
 
 using namespace qcd;
@@ -632,14 +670,50 @@ extern "C" int qcd_norm2(qcd_ctx* ctx, double* result, const void* a, int prec, 
   {
     LaunchScope ls(ctx, QCD_KC_BLAS, st);
     if (prec == QCD_PREC_SINGLE)
-      k_norm2<<<dim3(w->nblocks, nrhs), RED_THREADS, 0, st>>>((const float4*)a, w->v4, res, w->partials, w->counters,
-                                                             w->scal);
+      k_norm2<<<dim3(w->nblocks, nrhs), RED_THREADS, 0, st>>>((const float4*)a, w->v4, res, w->partials,
+                                                             w->counters);
     else
       k_norm2_f64<<<dim3(w->nblocks, nrhs), RED_THREADS, 0, st>>>((const double2*)a, (size_t)ctx->geom.vol * 12, res,
                                                                  w->partials, w->counters);
     check_launch();
   }
   QCD_CUDA_CHECK(cudaMemcpyAsync(result, res, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+  API_END(ctx)
+}
+
+// Same result as qcd_norm2, computed with the library's static scratch so that
+// the call allocates nothing (no cudaMalloc, no workspace growth).  For
+// callers that cannot allocate device memory at this point.
+extern "C" int qcd_norm2_noalloc(qcd_ctx* ctx, double* result, const void* a, int prec, int nrhs, void* stream) {
+  if (!ctx) return QCD_ERR_ARG;
+  API_BEGIN
+  QCD_REQUIRE(result && a, QCD_ERR_ARG, "qcd_norm2_noalloc: null pointer");
+  QCD_REQUIRE(nrhs >= 1 && nrhs <= NOALLOC_MAX_RHS, QCD_ERR_ARG,
+              "qcd_norm2_noalloc: nrhs must be between 1 and 16 (size of the static scratch)");
+  QCD_REQUIRE(prec == QCD_PREC_SINGLE || prec == QCD_PREC_DOUBLE, QCD_ERR_ARG,
+              "qcd_norm2_noalloc: SINGLE or DOUBLE");
+  cudaStream_t st = (cudaStream_t)stream;
+  NoAllocScratch* scr = noalloc_scratch_address();
+  int dev = 0, sms = 0;
+  QCD_CUDA_CHECK(cudaGetDevice(&dev));
+  QCD_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t v4 = (size_t)ctx->geom.vol * 6;
+  const int nblocks = std::max(1, std::min({4 * sms, NOALLOC_MAX_BLOCKS, (int)((v4 + RED_THREADS - 1) / RED_THREADS)}));
+  // the completion counters must start at zero; a previous call may have
+  // been interrupted, so clear them every time
+  QCD_CUDA_CHECK(cudaMemsetAsync(scr->counters, 0, sizeof(unsigned) * nrhs, st));
+  {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    if (prec == QCD_PREC_SINGLE)
+      k_norm2<<<dim3(nblocks, nrhs), RED_THREADS, 0, st>>>((const float4*)a, v4, scr->result, scr->partials,
+                                                          scr->counters);
+    else
+      k_norm2_f64<<<dim3(nblocks, nrhs), RED_THREADS, 0, st>>>((const double2*)a, (size_t)ctx->geom.vol * 12,
+                                                              scr->result, scr->partials, scr->counters);
+    check_launch();
+  }
+  QCD_CUDA_CHECK(cudaMemcpyAsync(result, scr->result, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   QCD_CUDA_CHECK(cudaStreamSynchronize(st));
   API_END(ctx)
 }
