@@ -222,6 +222,32 @@ int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int on_device,
  * max_inner 500, n_sap 4, n_jac 4, sap_prec SINGLE, use_graph 0. */
 int qcd_solve_params_default(qcd_solve_params* params);
 
+/* ---- ragged batches of lattices --------------------------------------- */
+
+typedef struct qcd_batch qcd_batch;
+
+/* Group n contexts (lattices that may differ in size, gauge field, kappa and
+ * c_SW; all on one device) for batched calls.  The batch does not own the
+ * contexts; destroy it before them. */
+int qcd_batch_create(int n, qcd_ctx* const* ctxs, qcd_batch** out);
+int qcd_batch_destroy(qcd_batch* batch);
+const char* qcd_batch_last_error(const qcd_batch* batch);
+
+/* out[i] = D_i in[i] (dagger = 0) or D_i^dag in[i] for every lattice of the
+ * batch in ONE kernel launch (float32 internal-layout fields of each
+ * context; App. A).  A work list gives each lattice a contiguous range of
+ * blocks. */
+int qcd_batch_apply_D(qcd_batch* batch, void* const* out, const void* const* in, int dagger, void* stream);
+
+/* Solve D_i x_i = b_i for every lattice (one right-hand side each, canonical
+ * float64 fields as in qcd_solve).  The lattices' solves run at the same
+ * time on one stream each (ordered after `stream`), so their kernels
+ * interleave on the GPU.  infos (may be NULL) receives one record per
+ * lattice; returns the first failing lattice's status, QCD_OK if all met
+ * params->tol. */
+int qcd_batch_solve(qcd_batch* batch, double* const* x, const double* const* b, int on_device,
+                    const qcd_solve_params* params, qcd_solve_info* infos, void* stream);
+
 /* ---- gradients -------------------------------------------------------- */
 
 /* Gradient of L = Re(eta^dag D^-1 b) (canonical float64 fields on the

@@ -81,6 +81,12 @@ _SIGS = {
     "qcd_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), _I]),
     "qcd_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "qcd_set_tuning": (_I, [_P, _I]),
+    "qcd_batch_create": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "qcd_batch_destroy": (_I, [_P]),
+    "qcd_batch_last_error": (ctypes.c_char_p, [_P]),
+    "qcd_batch_apply_D": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
+    "qcd_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.POINTER(SolveParams),
+                             ctypes.POINTER(SolveInfo), _P]),
     "qcd_tuning_report": (_I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
@@ -280,3 +286,41 @@ def qcd_tuning_report(ctx):
     buf = ctypes.create_string_buffer(4096)
     check(ctx, lib().qcd_tuning_report(ctx, buf, len(buf)))
     return buf.value.decode()
+
+
+def _batch_check(batch, rc):
+    if rc != QCD_OK:
+        raise QcdError(rc, lib().qcd_batch_last_error(batch).decode())
+    return rc
+
+
+def qcd_batch_create(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    out = ctypes.c_void_p()
+    rc = lib().qcd_batch_create(len(ctxs), arr, ctypes.byref(out))
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_batch_create failed")
+    return out
+
+
+def qcd_batch_destroy(batch):
+    return lib().qcd_batch_destroy(batch)
+
+
+def qcd_batch_apply_D(batch, outs, ins, dagger=0, stream=None):
+    o = (ctypes.c_void_p * len(outs))(*[_ptr(t) for t in outs])
+    i = (ctypes.c_void_p * len(ins))(*[_ptr(t) for t in ins])
+    return _batch_check(batch, lib().qcd_batch_apply_D(batch, o, i, int(dagger), _stream(stream)))
+
+
+def qcd_batch_solve(batch, xs, bs, params=None, stream=None, raise_on_error=True):
+    """Solve every lattice of the batch; returns (status, [SolveInfo])."""
+    p = params if params is not None else qcd_solve_params_default()
+    n = len(xs)
+    xa = (ctypes.c_void_p * n)(*[_ptr(t) for t in xs])
+    ba = (ctypes.c_void_p * n)(*[_ptr(t) for t in bs])
+    infos = (SolveInfo * n)()
+    rc = lib().qcd_batch_solve(batch, xa, ba, _on_device(bs[0]), ctypes.byref(p), infos, _stream(stream))
+    if raise_on_error and rc != QCD_OK:
+        raise QcdError(rc, lib().qcd_batch_last_error(batch).decode())
+    return rc, list(infos)

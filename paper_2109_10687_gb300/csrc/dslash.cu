@@ -88,13 +88,11 @@ __device__ __forceinline__ void hopping(const Geom& g, const SIO& in, const LP& 
 // budget); the autotuner picks among the instantiated shapes.  Blocks are
 // numbered rhs-fastest, so the nrhs blocks that share a tile of sites (and
 // its links and clover) run back to back and reuse them from L2.
-template <typename R, int MODE, int THREADS, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB)
-    dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in, typename Prec<R>::LP U,
-                  typename Prec<R>::CP clov, R kappa, int nrhs) {
-  const int rhs = blockIdx.x % nrhs;
-  const long long gid = (blockIdx.x / nrhs) * (long long)THREADS + threadIdx.x;
-  if (gid >= g.vol) return;
+// One site (lexicographic-domain index gid) of one right-hand side.
+template <typename R, int MODE>
+__device__ __forceinline__ void dslash_site(const Geom& g, const typename Prec<R>::SIO& out,
+                                            const typename Prec<R>::SIO& in, const typename Prec<R>::LP& U,
+                                            const typename Prec<R>::CP& clov, R kappa, long long gid, int rhs) {
   // domains are visited in lexicographic order, so that the neighbouring
   // domains whose surface spinors a domain reads are processed at about the
   // same time and their data is still in L2
@@ -119,6 +117,37 @@ __global__ void __launch_bounds__(THREADS, MINB)
       x.v[sp][c].im = fma(-kappa, acc.v[sp][c].im, x.v[sp][c].im);
     }
   out.store(g, dom + rhs_off, s, x);
+}
+
+template <typename R, int MODE, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+    dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in, typename Prec<R>::LP U,
+                  typename Prec<R>::CP clov, R kappa, int nrhs) {
+  const int rhs = blockIdx.x % nrhs;
+  const long long gid = (blockIdx.x / nrhs) * (long long)THREADS + threadIdx.x;
+  if (gid >= g.vol) return;
+  dslash_site<R, MODE>(g, out, in, U, clov, kappa, gid, rhs);
+}
+
+// Ragged batch: one launch over several lattices of different sizes.  Block
+// b belongs to the lattice whose [block_begin, block_end) range holds it.
+__global__ void __launch_bounds__(128, 4) dslash_batch_kernel(const BatchDesc* __restrict__ desc, int n, int dagger) {
+  int i = 0;
+  while (i + 1 < n && (long long)blockIdx.x >= desc[i + 1].block_begin) ++i;
+  const BatchDesc& d = desc[i];
+  const long long gid = ((long long)blockIdx.x - d.block_begin) * 128 + threadIdx.x;
+  if (gid >= d.g.vol) return;
+  const F32Spinor out{d.out}, in{(float4*)d.in};
+  const LinkPtr<float> U{d.u};
+  const CloverPtrF32 clov{d.clov};
+  if (dagger) dslash_site<float, MODE_DDAG>(d.g, out, in, U, clov, d.kappa, gid, 0);
+  else dslash_site<float, MODE_D>(d.g, out, in, U, clov, d.kappa, gid, 0);
+}
+
+void dslash_batch_launch(const BatchDesc* d_desc, int n, long long total_blocks, int dagger, cudaStream_t st) {
+  QCD_REQUIRE(total_blocks < (1LL << 31), QCD_ERR_ARG, "batch too large for one launch");
+  dslash_batch_kernel<<<(unsigned)total_blocks, 128, 0, st>>>(d_desc, n, dagger);
+  check_launch();
 }
 
 template <typename R>

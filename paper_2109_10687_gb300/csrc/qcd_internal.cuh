@@ -613,4 +613,16 @@ void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
 // dslash modes
 enum { MODE_D = 0, MODE_DDAG = 1, MODE_A = 2 };
 
+// one lattice of a ragged batch (device copy, rebuilt for every batched call)
+struct BatchDesc {
+  Geom g;
+  float4* out;
+  const float4* in;
+  const float2* u;
+  const float4* clov;
+  float kappa;
+  long long block_begin;  // first block of this lattice in the batched launch
+};
+void dslash_batch_launch(const BatchDesc* d_desc, int n, long long total_blocks, int dagger, cudaStream_t st);
+
 }  // namespace qcd
