@@ -1,0 +1,224 @@
+"""The other workloads of the solver, one JSON line each (``bench.py --config``).
+
+c1        8^4, eps 0.3, kappa 0.12, c_sw 1.0: float32 SAP-BiCGStab to relative
+          residual 1e-6 (the small solve).
+c3        48^4, eps 0.25, kappa 0.125, c_sw 1.1: the 12 spin-colour point
+          sources at the origin solved together (float16 SAP + float32
+          BiCGStab + float64 correction to 1e-10, graph-replayed iterations)
+          against 12 sequential plain float32 solves.
+c4        16^4, eps 0.3, kappa 0.12, c_sw 1.0: gradients of Re(eta^dag D^-1 b)
+          with respect to b and U (two solves + force kernels).
+c5        64^4, eps 0.2, kappa 0.126, c_sw 1.1: float32 Dslash roofline and the
+          mixed-precision solve to 1e-10.
+c5ragged  32 lattices with extents drawn from {8, 16} per direction,
+          kappa ~ U[0.115, 0.125], seeds 5000 + i: the batched operator in one
+          launch (GB/s) and the batched solve to 1e-10.
+All times are CUDA-event or synchronised wall times on one GPU; inputs are
+seeded and synthetic.
+"""
+
+import json
+import time
+
+import numpy as np
+import torch
+
+from bench import D_BYTES_PER_SITE, D_FLOP_PER_SITE, ClockSampler, measured_peaks
+
+
+def _lat(dims, eps, kappa, csw, seed, domain=(4, 4, 4, 4)):
+    from lattice_inputs import random_su3_field, random_su3_field_fast
+    from paper_2109_10687_gb300.lattice import Lattice
+    vol = int(np.prod(dims))
+    u = random_su3_field(dims, eps, seed) if vol <= 65536 else random_su3_field_fast(dims, eps, seed, "cuda")
+    lat = Lattice(dims, domain, -1, "chiral", "cuda:0").setup(u, kappa, csw)
+    return lat
+
+
+def _params(sap_prec="half", tol=1e-10, graph=1):
+    from paper_2109_10687_gb300 import binding as B
+    p = B.qcd_solve_params_default()
+    p.tol = tol
+    p.sap_prec = B.PREC_HALF if sap_prec == "half" else B.PREC_SINGLE
+    p.inner_tol = 1e-5 if sap_prec == "half" else 1e-6
+    p.max_inner = 2000
+    p.use_graph = graph
+    return p
+
+
+def _timed(fn, reps):
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t) / reps, out
+
+
+def _dslash_gbs(lat, b_dev, nrep=20):
+    from paper_2109_10687_gb300 import binding as B
+    a, o = lat.field("single"), lat.field("single")
+    B.qcd_import_spinor(lat.ctx, a, b_dev, B.PREC_SINGLE)
+    for _ in range(3):
+        B.qcd_apply_D(lat.ctx, o, a, B.PREC_SINGLE)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(nrep):
+        B.qcd_apply_D(lat.ctx, o, a, B.PREC_SINGLE)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nrep
+    vol = int(np.prod(lat.dims))
+    peak, kind = measured_peaks()
+    gbs = D_BYTES_PER_SITE * vol / (ms * 1e-3) / 1e9
+    return {"ms": ms, "gbs": gbs, "gflops": D_FLOP_PER_SITE * vol / (ms * 1e-3) / 1e9, "frac_of_hbm": gbs / peak,
+            "peak_gbs": peak, "peak_kind": kind}
+
+
+def c1(args):
+    from lattice_inputs import gaussian_spinor
+    from paper_2109_10687_gb300 import binding as B
+    dims = (8, 8, 8, 8)
+    lat = _lat(dims, 0.3, 0.12, 1.0, 1001)
+    b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2001))).cuda().contiguous()
+    x = torch.zeros_like(b)
+    res = {}
+    for name, p in (("plain_f32", _params("single", 1e-6, 0)), ("plain_f32_graph", _params("single", 1e-6, 1)),
+                    ("mixed_f16_graph", _params("half", 1e-6, 1))):
+        for _ in range(3):
+            B.qcd_solve(lat.ctx, x, b, 1, p)
+        t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, p), max(3, args.steps))
+        res[name] = {"ms": 1e3 * t, "inner": info.inner_iters, "outer": info.outer_iters,
+                     "true_resid": info.true_resid}
+    return {"config": {"workload": "8^4, eps 0.3, kappa 0.12, c_sw 1.0, one Gaussian source, 4^4 domains, "
+                                   "n_sap 4, n_jac 4, FP32 SAP-BiCGStab to relative residual 1e-6"},
+            "metric": "time to relative residual 1e-6", "unit": "ms", "results": res}
+
+
+def c3(args):
+    from lattice_inputs import point_source
+    from paper_2109_10687_gb300 import binding as B
+    dims = (48, 48, 48, 48)
+    lat = _lat(dims, 0.25, 0.125, 1.1, 1301)
+    srcs = np.stack([point_source(dims, c, s) for c in range(3) for s in range(4)])
+    b = torch.view_as_real(torch.from_numpy(srcs)).cuda().contiguous()
+    x = torch.zeros_like(b)
+    out = {}
+    clk = ClockSampler("0")
+    clk.start()
+    # warm (allocations, tuning) then time the batched mixed solve
+    B.qcd_solve(lat.ctx, x, b, 12, _params("half"))
+    t_batch, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 12, _params("half")), 1)
+    out["batched_mixed"] = {"s": t_batch, "inner": info.inner_iters, "outer": info.outer_iters,
+                            "true_resid": info.true_resid, "status": rc}
+    # 12 sequential plain float32 solves of the same sources
+    b1 = [b[i].contiguous() for i in range(12)]
+    x1 = torch.zeros_like(b1[0])
+    B.qcd_solve(lat.ctx, x1, b1[0], 1, _params("single", graph=0))
+    t0 = time.perf_counter()
+    worst = 0.0
+    iters = 0
+    for i in range(12):
+        rc, info = B.qcd_solve(lat.ctx, x1, b1[i], 1, _params("single", graph=0))
+        worst = max(worst, info.true_resid)
+        iters += info.inner_iters
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    out["sequential_plain_f32"] = {"s": t_seq, "inner_total": iters, "true_resid": worst}
+    out["speedup"] = t_seq / t_batch
+    out["clocks"] = clk.stop()
+    return {"config": {"workload": "48^4, eps 0.25, kappa 0.125, c_sw 1.1, 12 spin-colour point sources at the "
+                                   "origin; batched float16-SAP + float32 BiCGStab + float64 correction to 1e-10 "
+                                   "(graph-replayed iterations) vs 12 sequential plain float32 solves"},
+            "metric": "time to FP64 residual 1e-10 for 12 right-hand sides", "unit": "s", "results": out}
+
+
+def c4(args):
+    from lattice_inputs import gaussian_spinor
+    from paper_2109_10687_gb300 import binding as B
+    dims = (16, 16, 16, 16)
+    lat = _lat(dims, 0.3, 0.12, 1.0, 1401)
+    eta = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 3001))).cuda().contiguous()
+    b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 3002))).cuda().contiguous()
+    gb = torch.zeros_like(b)
+    gu = torch.zeros(lat.site_shape + (4, 3, 3, 2), dtype=torch.float64, device="cuda")
+    p = _params("half")
+    B.qcd_grad(lat.ctx, eta, b, gb, gu, project=1, params=p)
+    t, _ = _timed(lambda: B.qcd_grad(lat.ctx, eta, b, gb, gu, project=1, params=p), max(3, args.steps))
+    return {"config": {"workload": "16^4, eps 0.3, kappa 0.12, c_sw 1.0: gradients of Re(eta^dag D^-1 b) wrt b and "
+                                   "U (su(3)-projected), two mixed-precision solves + force kernels"},
+            "metric": "time per gradient", "unit": "ms", "results": {"ms": 1e3 * t}}
+
+
+def c5(args):
+    from lattice_inputs import gaussian_spinor
+    from paper_2109_10687_gb300 import binding as B
+    dims = (64, 64, 64, 64)
+    lat = _lat(dims, 0.2, 0.126, 1.1, 1501)
+    b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2501))).cuda().contiguous()
+    clk = ClockSampler("0")
+    clk.start()
+    d = _dslash_gbs(lat, b)
+    x = torch.zeros_like(b)
+    B.qcd_solve(lat.ctx, x, b, 1, _params("half"))
+    t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, _params("half")), 2)
+    tf, (rcf, infof) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, _params("single")), 1)
+    return {"config": {"workload": "64^4, eps 0.2, kappa 0.126, c_sw 1.1, one Gaussian source"},
+            "metric": "Dslash GB/s; time to FP64 residual 1e-10", "unit": "GB/s; s",
+            "results": {"dslash": d, "mixed_solve_s": t, "inner": info.inner_iters, "outer": info.outer_iters,
+                        "true_resid": info.true_resid, "plain_f32_solve_s": tf, "plain_inner": infof.inner_iters,
+                        "clocks": clk.stop()}}
+
+
+def c5ragged(args):
+    from lattice_inputs import gaussian_spinor
+    from paper_2109_10687_gb300 import binding as B
+    rng = np.random.default_rng(5000)
+    lats, bs, ins, outs, vols = [], [], [], [], []
+    for i in range(32):
+        dims = tuple(int(v) for v in rng.choice([8, 16], size=4))
+        kappa = float(rng.uniform(0.115, 0.125))
+        lat = _lat(dims, 0.3, kappa, 1.0, 5000 + i)
+        b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 7000 + i))).cuda().contiguous()
+        a = lat.field("single")
+        B.qcd_import_spinor(lat.ctx, a, b, B.PREC_SINGLE)
+        lats.append(lat)
+        bs.append(b)
+        ins.append(a)
+        outs.append(lat.field("single"))
+        vols.append(int(np.prod(dims)))
+    bt = B.qcd_batch_create([l.ctx for l in lats])
+    for _ in range(3):
+        B.qcd_batch_apply_D(bt, outs, ins)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    nrep = 20
+    for _ in range(nrep):
+        B.qcd_batch_apply_D(bt, outs, ins)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nrep
+    peak, kind = measured_peaks()
+    total = sum(vols)
+    gbs = D_BYTES_PER_SITE * total / (ms * 1e-3) / 1e9
+    xs = [torch.zeros_like(b) for b in bs]
+    B.qcd_batch_solve(bt, xs, bs, _params("half"))
+    t, (rc, infos) = _timed(lambda: B.qcd_batch_solve(bt, xs, bs, _params("half")), 1)
+    B.qcd_batch_destroy(bt)
+    return {"config": {"workload": "ragged batch of 32 lattices, extents from {8, 16} per direction, eps 0.3, "
+                                   "kappa ~ U[0.115, 0.125], c_sw 1.0, seeds 5000 + i", "sites": total},
+            "metric": "batched Dslash GB/s (one launch); batched solve time to 1e-10", "unit": "GB/s; s",
+            "results": {"dslash_batched": {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak, "peak_kind": kind},
+                        "batched_solve_s": t, "status": rc, "worst_true_resid": max(i.true_resid for i in infos),
+                        "inner_max": max(i.inner_iters for i in infos)}}
+
+
+def run(args):
+    torch.cuda.set_device(0)
+    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "c5ragged": c5ragged}[args.config]
+    line = fn(args)
+    line["name"] = args.config
+    print(json.dumps(line))
