@@ -81,10 +81,10 @@ def random_su3_field_fast(dims, eps, seed, device="cuda", chunk=1 << 21):
     out = np.empty((coef.shape[0], 3, 3), dtype=np.complex128)
     for a in range(0, coef.shape[0], chunk):
         c = torch.from_numpy(coef[a:a + chunk]).to(device=device, dtype=torch.complex128)
-        h = torch.einsum("na,aij->nij", c, lam)
+        h = (c @ lam.reshape(8, 9)).reshape(-1, 3, 3)
         w, v = torch.linalg.eigh(h)
         ph = torch.exp(1j * float(eps) * w.to(torch.complex128))
-        u = torch.einsum("nij,nj,nkj->nik", v, ph, v.conj())
+        u = (v * ph.unsqueeze(-2)) @ v.conj().transpose(-1, -2)
         out[a:a + chunk] = u.cpu().numpy()
     return out.reshape(shape + (4, 3, 3))
 
