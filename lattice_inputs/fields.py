@@ -67,7 +67,7 @@ def random_su3_field(dims, eps, seed):
     return u
 
 
-def random_su3_field_fast(dims, eps, seed, device="cuda", chunk=1 << 21):
+def random_su3_field_fast(dims, eps, seed, device="cuda", chunk=1 << 15):
     """Same draws as ``random_su3_field``; the exponential exp(i eps H) is taken
     on ``device`` with torch's batched Hermitian eigendecomposition (float64),
     in chunks of ``chunk`` links, which makes 48^4 and 64^4 fields practical.

@@ -358,7 +358,7 @@ extern "C" int qcd_destroy(qcd_ctx* ctx) {
   tuner_free(ctx);
   void* ptrs[] = {ctx->d_nbr, ctx->d_lex2dom, ctx->d_tflag, ctx->u64, ctx->u32, ctx->u16, ctx->clov64,
                   ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status,
-                  ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32};
+                  ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32, ctx->udf, ctx->clovdf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
@@ -437,6 +437,7 @@ extern "C" int qcd_build_clover(qcd_ctx* ctx, void* stream) {
   QCD_CUDA_CHECK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   build_clover_launch(ctx, st);
   build_sap_staging(ctx, st);
+  build_df64_copies(ctx, true, true, st);
   int hs = 0;
   QCD_CUDA_CHECK(cudaMemcpyAsync(&hs, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   QCD_CUDA_CHECK(cudaStreamSynchronize(st));

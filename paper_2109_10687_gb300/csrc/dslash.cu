@@ -29,6 +29,13 @@ struct Prec<double> {
   using CP = CloverPtrF64;
   using CB = CloverBlockF64;
 };
+template <>
+struct Prec<df64> {
+  using SIO = DF64Spinor;
+  using LP = LinkPtr<df64>;
+  using CP = CloverPtrDF64;
+  using CB = CloverBlockDF64;
+};
 
 // acc += hop in direction MU (both orientations); PMF / PMB are the projector
 // signs of the forward and backward hop.  FILTER: 0 all hops, 1 only hops
@@ -48,7 +55,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const SIO& in, const LP& 
       SU3<R> u;
       U.load(g, dom, MU, s, u);
       su3_mul(u, h, uh);
-      if (sign < 0) scale_half(uh, R(-1));
+      if (sign < 0) scale_half(uh, R(-1.0f));
       accumulate<MU, PMF>(acc, uh);
     }
   }
@@ -64,7 +71,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const SIO& in, const LP& 
       SU3<R> u;
       U.load(g, nd, MU, ns, u);
       su3_dag_mul(u, h, uh);
-      if (sign < 0) scale_half(uh, R(-1));
+      if (sign < 0) scale_half(uh, R(-1.0f));
       accumulate<MU, PMB>(acc, uh);
     }
   }
@@ -217,7 +224,13 @@ static const char* kDslashShapes[] = {"128x4", "128x5", "128x6", "256x2"};
 
 void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st) {
   const Geom& g = ctx->geom;
-  if (prec == QCD_PREC_DOUBLE) {
+  if (prec == PREC_DF64) {
+    QCD_REQUIRE(mode == MODE_D, QCD_ERR_ARG, "the double-float operator provides D only");
+    QCD_REQUIRE(ctx->udf && ctx->clovdf, QCD_ERR_STATE, "double-float copies not built");
+    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+    launch_dslash_shape<df64, MODE_D, 128, 2>(g, out, in, ctx->udf, ctx->clovdf, df64(ctx->kappa), nrhs, st);
+    check_launch();
+  } else if (prec == QCD_PREC_DOUBLE) {
     QCD_REQUIRE(mode != MODE_A, QCD_ERR_ARG, "A is provided in float32 only");
     LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
     if (mode == MODE_D)
@@ -271,6 +284,33 @@ void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col
                                                       LinkPtr<float>{ctx->u32}, CloverPtrF32{ctx->cinv32},
                                                       (float)ctx->kappa, row, col);
   check_launch();
+}
+
+// float64 (double2) fields -> double-float (float4) copies, elementwise
+__global__ void f64_to_df64_kernel(const double2* __restrict__ in, float4* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    const df64 re(v.x), im(v.y);
+    out[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
+void build_df64_copies(qcd_ctx* ctx, bool links, bool clover, cudaStream_t st) {
+  const Geom& g = ctx->geom;
+  if (links) {
+    const size_t n = (size_t)g.vol * 36;
+    if (!ctx->udf) QCD_CUDA_CHECK(cudaMalloc(&ctx->udf, n * sizeof(float4)));
+    LaunchScope ls(ctx, QCD_KC_OTHER, st);
+    f64_to_df64_kernel<<<1024, 256, 0, st>>>(ctx->u64, ctx->udf, n);
+    check_launch();
+  }
+  if (clover) {
+    const size_t n = (size_t)g.vol * 36;
+    if (!ctx->clovdf) QCD_CUDA_CHECK(cudaMalloc(&ctx->clovdf, n * sizeof(float4)));
+    LaunchScope ls(ctx, QCD_KC_OTHER, st);
+    f64_to_df64_kernel<<<1024, 256, 0, st>>>(ctx->clov64, ctx->clovdf, n);
+    check_launch();
+  }
 }
 
 }  // namespace qcd

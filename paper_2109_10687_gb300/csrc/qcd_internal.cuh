@@ -36,6 +36,7 @@
 #include <string>
 
 #include "qcd_gb300.h"
+#include "df64.cuh"
 
 namespace qcd {
 
@@ -437,6 +438,44 @@ struct LinkPtrHalf {
   }
 };
 
+// double-float storage (the float64 residual of the solve): float4 =
+// (re.hi, re.lo, im.hi, im.lo) per complex, same element order as float64
+struct DF64Spinor {
+  float4* p;
+  __device__ __forceinline__ size_t idx(const Geom& g, int dom, int comp, int s) const {
+    return ((size_t)(dom * 12 + comp) << g.logvd) + s;
+  }
+  __device__ __forceinline__ void load(const Geom& g, int dom, int s, Spinor<df64>& a) const {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4 v = __ldg(p + idx(g, dom, sp * 3 + c, s));
+        a.v[sp][c] = make_cx(df64(v.x, v.y), df64(v.z, v.w));
+      }
+  }
+  __device__ __forceinline__ void store(const Geom& g, int dom, int s, const Spinor<df64>& a) const {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        p[idx(g, dom, sp * 3 + c, s)] =
+            make_float4(a.v[sp][c].re.hi, a.v[sp][c].re.lo, a.v[sp][c].im.hi, a.v[sp][c].im.lo);
+  }
+};
+template <>
+struct LinkPtr<df64> {
+  const float4* p;
+  __device__ __forceinline__ void load(const Geom& g, int dom, int mu, int s, SU3<df64>& u) const {
+    const size_t base = ((size_t)((dom * 4 + mu) * 9)) << g.logvd;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float4 v = __ldg(p + base + ((size_t)e << g.logvd) + s);
+      u.m[e / 3][e % 3] = make_cx(df64(v.x, v.y), df64(v.z, v.w));
+    }
+  }
+};
+
 // packed clover block readers (block b = 0 upper, 1 lower)
 struct CloverBlockF32 {
   float r[36];
@@ -448,6 +487,23 @@ struct CloverBlockF64 {
   double r[36];
   __device__ __forceinline__ cx<double> diag(int i) const { return make_cx(r[i], 0.0); }
   __device__ __forceinline__ cx<double> off(int k) const { return make_cx(r[6 + 2 * k], r[7 + 2 * k]); }
+};
+
+struct CloverBlockDF64 {
+  df64 r[36];
+  __device__ __forceinline__ cx<df64> diag(int i) const { return make_cx(r[i], df64(0.f)); }
+  __device__ __forceinline__ cx<df64> off(int k) const { return make_cx(r[6 + 2 * k], r[7 + 2 * k]); }
+};
+struct CloverPtrDF64 {
+  const float4* p;  // [dom][36][vd]: two reals of the packed block per float4
+  __device__ __forceinline__ void load_block(const Geom& g, int dom, int s, int b, CloverBlockDF64& blk) const {
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      const float4 v = __ldg(p + (((size_t)(dom * 36 + 18 * b + k)) << g.logvd) + s);
+      blk.r[2 * k] = df64(v.x, v.y);
+      blk.r[2 * k + 1] = df64(v.z, v.w);
+    }
+  }
 };
 
 struct CloverPtrF32 {
@@ -524,6 +580,8 @@ struct qcd_ctx {
   double2* cinv64 = nullptr;     // (1 + C)^-1
   float4* cinv32 = nullptr;
   __half2* cinv16 = nullptr;
+  float4* udf = nullptr;         // links in double-float
+  float4* clovdf = nullptr;      // 1 + C in double-float
   int* d_status = nullptr;       // device status word (non-finite, ...)
   cudaStream_t aux_stream = nullptr;  // private stream for graph capture
   // staging layouts of the shared-memory SAP kernel (4^4 domains only)
@@ -612,6 +670,9 @@ void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
 
 // dslash modes
 enum { MODE_D = 0, MODE_DDAG = 1, MODE_A = 2 };
+// internal precision code of the double-float operator (not part of the ABI)
+constexpr int PREC_DF64 = 3;
+void build_df64_copies(qcd_ctx* ctx, bool links, bool clover, cudaStream_t st);
 
 // one lattice of a ragged batch (device copy, rebuilt for every batched call)
 struct BatchDesc {
