@@ -458,6 +458,78 @@ __global__ void k_f64_axpy_f32(Geom g, double2* x, const float4* __restrict__ q,
 }
 
 // ---------------------------------------------------------------------------
+// double-float versions of the Algorithm-4 vector kernels (float4 per
+// complex: re.hi, re.lo, im.hi, im.lo; same element order as float64)
+// ---------------------------------------------------------------------------
+// elementwise, in place allowed: float64 -> double-float
+__global__ void k_df_from_f64(const double2* in, float4* out, size_t n2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    const df64 re(v.x), im(v.y);
+    out[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+// elementwise, in place allowed: double-float -> float64
+__global__ void k_f64_from_df(const float4* in, double2* out, size_t n2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    out[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+}
+// r = b - r (r holds D x on entry), in double-float; out[rhs] = |r|^2 (float64 sums)
+__global__ void k_residual_df(const float4* __restrict__ b, float4* r, size_t n2, double* out, double* partials,
+                              unsigned* counters) {
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * n2;
+  double* part = partials + (size_t)rhs * MAX_RED_OUT * gridDim.x;
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 bv = b[off + i], dv = r[off + i];
+    const df64 re = df64(bv.x, bv.y) - df64(dv.x, dv.y);
+    const df64 im = df64(bv.z, bv.w) - df64(dv.z, dv.w);
+    r[off + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    const double dr = to_double(re), di = to_double(im);
+    s = fma(dr, dr, fma(di, di, s));
+  }
+  double v[1] = {s}, tot[1];
+  if (grid_reduce<1>(v, part, counters + rhs, tot) && threadIdx.x == 0) out[rhs] = tot[0];
+}
+// float32 p = R_SP(r / err) from a double-float r
+__global__ void k_df_to_f32_scaled(Geom g, const float4* __restrict__ r, float4* p, const double* scale) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int rhs = blockIdx.y;
+  const int dom = (int)(gid >> g.logvd) + rhs * g.ndom, s = (int)(gid & (g.vd - 1));
+  const double f = scale[rhs];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 a = r[((size_t)(dom * 12 + 2 * k) << g.logvd) + s];
+    const float4 b = r[((size_t)(dom * 12 + 2 * k + 1) << g.logvd) + s];
+    p[((size_t)(dom * 6 + k) << g.logvd) + s] =
+        make_float4((float)(((double)a.x + a.y) * f), (float)(((double)a.z + a.w) * f),
+                    (float)(((double)b.x + b.y) * f), (float)(((double)b.z + b.w) * f));
+  }
+}
+// double-float x += err * P_DP(q32)
+__global__ void k_df_axpy_f32(Geom g, float4* x, const float4* __restrict__ q, const double* scale) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int rhs = blockIdx.y;
+  const int dom = (int)(gid >> g.logvd) + rhs * g.ndom, s = (int)(gid & (g.vd - 1));
+  const df64 f(scale[rhs]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 v = q[((size_t)(dom * 6 + k) << g.logvd) + s];
+    float4& a = x[((size_t)(dom * 12 + 2 * k) << g.logvd) + s];
+    float4& b = x[((size_t)(dom * 12 + 2 * k + 1) << g.logvd) + s];
+    const df64 ar = fma(f, df64(v.x), df64(a.x, a.y)), ai = fma(f, df64(v.y), df64(a.z, a.w));
+    const df64 br = fma(f, df64(v.z), df64(b.x, b.y)), bi = fma(f, df64(v.w), df64(b.z, b.w));
+    a = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+    b = make_float4(br.hi, br.lo, bi.hi, bi.lo);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
 struct Launcher {
@@ -636,6 +708,7 @@ extern "C" int qcd_solve_params_default(qcd_solve_params* p) {
   p->sap_prec = QCD_PREC_SINGLE;
   p->use_graph = 0;
   p->x_is_guess = 0;
+  p->residual_prec = 0;
   return QCD_OK;
 }
 
@@ -779,17 +852,40 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     k_norm2_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, n2, d_red, w->partials, w->counters);
     check_launch();
   }
+  // residual precision: double-float on the float32 pipes (default) or float64
+  const bool df = P.residual_prec == 0;
+  float4* bdf = reinterpret_cast<float4*>(w->t64);
+  float4* xdf = reinterpret_cast<float4*>(w->x64);
+  float4* rdf = reinterpret_cast<float4*>(w->r64);
+  const size_t n2all = n2 * nrhs;
+  if (df) {
+    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+    k_df_from_f64<<<1024, 256, 0, st>>>(w->b64, bdf, n2all);
+    check_launch();
+  }
   if (P.x_is_guess) {
     rc = qcd_import_spinor(ctx, w->x64, x, QCD_PREC_DOUBLE, nrhs, on_device, stream);
     if (rc != QCD_OK) throw Error{rc, ctx->err};
+    if (df) {
+      LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+      k_df_from_f64<<<1024, 256, 0, st>>>(w->x64, xdf, n2all);
+      check_launch();
+    }
   } else {
     QCD_CUDA_CHECK(cudaMemsetAsync(w->x64, 0, n2 * sizeof(double2) * nrhs, st));
   }
   auto residual = [&]() {
-    dslash_launch(ctx, w->r64, w->x64, QCD_PREC_DOUBLE, MODE_D, nrhs, st);
-    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-    k_residual_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, w->r64, n2, d_red + nrhs, w->partials, w->counters);
-    check_launch();
+    if (df) {
+      dslash_launch(ctx, rdf, xdf, PREC_DF64, MODE_D, nrhs, st);
+      LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+      k_residual_df<<<rgrid, RED_THREADS, 0, st>>>(bdf, rdf, n2, d_red + nrhs, w->partials, w->counters);
+      check_launch();
+    } else {
+      dslash_launch(ctx, w->r64, w->x64, QCD_PREC_DOUBLE, MODE_D, nrhs, st);
+      LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+      k_residual_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, w->r64, n2, d_red + nrhs, w->partials, w->counters);
+      check_launch();
+    }
     QCD_CUDA_CHECK(cudaMemcpyAsync(h_r2.data(), d_red + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaStreamSynchronize(st));
   };
@@ -797,7 +893,8 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     residual();
   } else {
     // x = 0: r = b exactly, no operator application needed
-    QCD_CUDA_CHECK(cudaMemcpyAsync(w->r64, w->b64, n2 * sizeof(double2) * nrhs, cudaMemcpyDeviceToDevice, st));
+    QCD_CUDA_CHECK(cudaMemcpyAsync(w->r64, df ? (const void*)bdf : (const void*)w->b64, n2 * sizeof(double2) * nrhs,
+                                   cudaMemcpyDeviceToDevice, st));
     QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + nrhs, d_red, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, st));
     QCD_CUDA_CHECK(cudaMemcpyAsync(h_r2.data(), d_red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   }
@@ -829,7 +926,8 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     {
       LaunchScope ls(ctx, QCD_KC_BLAS, st);
-      k_f64_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, w->r64, w->tmp32, d_red + 2 * nrhs);
+      if (df) k_df_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, rdf, w->tmp32, d_red + 2 * nrhs);
+      else k_f64_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, w->r64, w->tmp32, d_red + 2 * nrhs);
       check_launch();
     }
     clover_apply_launch(ctx, w->tmp32, w->tmp32, QCD_PREC_SINGLE, 1, nrhs, st);
@@ -846,10 +944,16 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     {
       LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-      k_f64_axpy_f32<<<sgrid, 128, 0, st>>>(g, w->x64, w->x, d_red + 2 * nrhs);
+      if (df) k_df_axpy_f32<<<sgrid, 128, 0, st>>>(g, xdf, w->x, d_red + 2 * nrhs);
+      else k_f64_axpy_f32<<<sgrid, 128, 0, st>>>(g, w->x64, w->x, d_red + 2 * nrhs);
       check_launch();
     }
     residual();
+  }
+  if (df) {
+    LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+    k_f64_from_df<<<1024, 256, 0, st>>>(xdf, w->x64, n2all);
+    check_launch();
   }
   rc = qcd_export_spinor(ctx, x, w->x64, QCD_PREC_DOUBLE, nrhs, on_device, stream);
   if (rc != QCD_OK) throw Error{rc, ctx->err};

@@ -47,6 +47,17 @@ def test_solve_to_1e10(c1, c1_ref, sap_prec, use_graph):
     assert 1 <= info.outer_iters <= 6
 
 
+@pytest.mark.parametrize("residual_prec", [0, 1])
+def test_solve_residual_precisions(c1, c1_ref, residual_prec):
+    """Algorithm 4 with its residual in double-float (0) or native float64 (1)."""
+    b, x_ref = c1_ref
+    x, rc, info = c1.lat.solve(b, tol=1e-10, sap_prec="half", inner_tol=1e-5, residual_prec=residual_prec)
+    x = to_np(x)
+    assert rc == 0
+    assert true_resid(c1.op, x, b) < 1e-10
+    assert rel_l2(x, x_ref) < 1e-8
+
+
 def test_solve_host_buffers(c1, c1_ref):
     b, x_ref = c1_ref
     x, rc, info = c1.lat.solve(b, host=True, tol=1e-10)
