@@ -63,6 +63,29 @@ def sap_bytes_per_site(prec):
     return sum(seq) / len(seq)
 
 
+def sap_flop_per_site():
+    """Flop per site of one SAP half-sweep launch, averaged over the launches
+    of one M_SAP, in the per-site constants of the paper's flop accounting for
+    4^4 domains in the chiral basis (168 flop per hop in every direction,
+    600 flop for C_inv and the axpy, 48 flop for the residual update):
+    f_in = 600 + 8 * (3/4) * 168 = 1608 per A_cc application (n_jac Jacobi
+    sweeps + one for the update), f_out = 2 * 168 + 600 * 15/16 = 898.5 for
+    the surface term."""
+    f_in = 600 + 8 * 0.75 * 168
+    f_out = 2 * 168 + 600 * 15 / 16
+    seq = []
+    for sweep in range(N_SAP + 1):
+        last = sweep == N_SAP
+        for colour in (0, 1):
+            has_surf = not (sweep == 0 and colour == 0)
+            seq.append((f_out if has_surf else 0) + N_JAC * f_in + (0 if last else f_in + 48))
+    return sum(seq) / len(seq)
+
+
+# float32 peak of the CUDA cores: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -400,6 +423,7 @@ def main():
     sap_avg_ms = sap_ms / max(1, sap_n)
     sap_bytes = sap_bytes_per_site("half") * vol / 2
     sap_gbs = sap_bytes / (sap_avg_ms * 1e-3) / 1e9
+    sap_tflops = sap_flop_per_site() * (vol / 2) / (sap_avg_ms * 1e-3) / 1e12
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "sap_block_traffic.json")
     if os.path.exists(tfile):
@@ -425,11 +449,13 @@ def main():
         "dslash": {"kernel": "dslash_kernel<float, D>", "ms": d_ms, "gbs": d_gbs, "gflops": d_gflops,
                    "bytes_per_site": D_BYTES_PER_SITE, "flop_per_site": D_FLOP_PER_SITE,
                    "frac_of_hbm": d_gbs / peak, "peak_gbs": peak, "peak_kind": peak_kind},
-        "roofline": {"kernel": "sap_block_kernel<F16>", "bound": "hbm", "achieved": sap_gbs, "peak": peak,
-                     "unit": "GB/s", "frac": sap_gbs / peak, "traffic": traffic,
-                     "bytes_per_site": sap_bytes_per_site("half"), "sites_per_launch": vol // 2,
+        "roofline": {"kernel": "sap_staged_kernel<float16 storage>", "bound": "alu", "achieved": sap_tflops,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": sap_tflops / FP32_PEAK_TFLOPS,
+                     "traffic": traffic, "flop_per_site": sap_flop_per_site(), "sites_per_launch": vol // 2,
                      "avg_launch_ms": sap_avg_ms, "share_of_device_time": sap_ms / total_ms if total_ms else None,
-                     "peak_kind": peak_kind},
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "hbm_view": {"bytes_per_site": sap_bytes_per_site("half"), "achieved_gbs": sap_gbs,
+                                  "frac_of_measured": sap_gbs / peak}},
         "kernel_classes_ms": {name: prof[k][1] for k, name in
                               ((B.KC_DSLASH, "dslash_A"), (B.KC_SAP_BLOCK, "sap_block"), (B.KC_BLAS, "blas"),
                                (B.KC_DOUBLE, "float64"), (B.KC_OTHER, "other"))},

@@ -83,8 +83,8 @@ typedef struct qcd_solve_params {
   int use_graph;       /* 1: replay each BiCGStab iteration as a CUDA graph  */
   int x_is_guess;      /* 1: x holds an initial guess on entry (resume)      */
   int residual_prec;   /* precision of x, r = b - D x and D in Algorithm 4:
-                          0 double-float (two float32, ~48 bits, on the
-                          float32 pipes; default), 1 native float64          */
+                          1 native float64 (default), 0 double-float (two
+                          float32, ~48 bits, on the float32 pipes)           */
 } qcd_solve_params;
 
 /* Results of qcd_solve, one entry per right-hand side where indicated. */
@@ -223,7 +223,7 @@ int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int on_device,
 
 /* Fill params with defaults: tol 1e-10, inner_tol 1e-6, max_outer 20,
  * max_inner 500, n_sap 4, n_jac 4, sap_prec SINGLE, use_graph 0,
- * residual_prec 0 (double-float). */
+ * residual_prec 1 (float64). */
 int qcd_solve_params_default(qcd_solve_params* params);
 
 /* ---- ragged batches of lattices --------------------------------------- */

@@ -708,7 +708,7 @@ extern "C" int qcd_solve_params_default(qcd_solve_params* p) {
   p->sap_prec = QCD_PREC_SINGLE;
   p->use_graph = 0;
   p->x_is_guess = 0;
-  p->residual_prec = 0;
+  p->residual_prec = 1;
   return QCD_OK;
 }
 
@@ -852,7 +852,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     k_norm2_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, n2, d_red, w->partials, w->counters);
     check_launch();
   }
-  // residual precision: double-float on the float32 pipes (default) or float64
+  // residual precision: native float64 (default) or double-float on the float32 pipes
   const bool df = P.residual_prec == 0;
   float4* bdf = reinterpret_cast<float4*>(w->t64);
   float4* xdf = reinterpret_cast<float4*>(w->x64);
