@@ -37,6 +37,10 @@ struct Prec<df64> {
   using CB = CloverBlockDF64;
 };
 
+__global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
+                                                                LinkPtr<df64> U, CloverPtrDF64 clov, df64 kappa,
+                                                                int nrhs);
+
 // acc += hop in direction MU (both orientations); PMF / PMB are the projector
 // signs of the forward and backward hop.  FILTER: 0 all hops, 1 only hops
 // inside the domain, 2 only hops that leave the domain.
@@ -228,7 +232,11 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
     QCD_REQUIRE(mode == MODE_D, QCD_ERR_ARG, "the double-float operator provides D only");
     QCD_REQUIRE(ctx->udf && ctx->clovdf, QCD_ERR_STATE, "double-float copies not built");
     LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-    launch_dslash_shape<df64, MODE_D, 128, 2>(g, out, in, ctx->udf, ctx->clovdf, df64(ctx->kappa), nrhs, st);
+    const long long blocks = (long long)((g.vol + 63) / 64) * nrhs;
+    QCD_REQUIRE(blocks < (1LL << 31), QCD_ERR_ARG, "lattice too large for one launch");
+    dslash_df64_split_kernel<<<(unsigned)blocks, dim3(32, 3, 2), 0, st>>>(
+        g, DF64Spinor{(float4*)out}, DF64Spinor{(float4*)in}, LinkPtr<df64>{ctx->udf}, CloverPtrDF64{ctx->clovdf},
+        df64(ctx->kappa), nrhs);
     check_launch();
   } else if (prec == QCD_PREC_DOUBLE) {
     QCD_REQUIRE(mode != MODE_A, QCD_ERR_ARG, "A is provided in float32 only");
@@ -284,6 +292,150 @@ void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col
                                                       LinkPtr<float>{ctx->u32}, CloverPtrF32{ctx->cinv32},
                                                       (float)ctx->kappa, row, col);
   check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// D in double-float with the work of a site split over its three colour rows
+// ---------------------------------------------------------------------------
+// Thread (site, a) forms row a of every hop product U h and of the clover
+// multiply, so a thread holds one colour of the accumulator (4 spins) instead
+// of all twelve components; three times as many threads with a third of the
+// live state keep the long double-float dependency chains overlapped.
+// Block (32, 3, 2): warps of 32 consecutive sites share one colour row.
+template <int MU, bool FWD>
+__device__ __forceinline__ void df_hop(const Geom& g, const DF64Spinor& in, const LinkPtr<df64>& U, int dom, int s,
+                                       int a, cx<df64> acc[4]) {
+  int nd, ns;
+  const int sign = nbr_site(g, dom, s, MU, FWD, nd, ns);
+  constexpr int PM = FWD ? -1 : +1;
+  // projected neighbour, all colours: h[spin row][colour]
+  HalfSpinor<df64> h;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Spinor<df64> p;  // only colour c of the spinor is filled
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const float4 v = __ldg(in.p + in.idx(g, nd, sp * 3 + c, ns));
+      p.v[sp][c] = make_cx(df64(v.x, v.y), df64(v.z, v.w));
+    }
+    // project colour c only (the projector acts on spin, colour by colour)
+    const cx<df64> u0 = p.v[0][c], u1 = p.v[1][c], l0 = p.v[2][c], l1 = p.v[3][c];
+    if (MU == 0) {
+      if (PM < 0) { h.h[0][c] = u0 + times_i(l1); h.h[1][c] = u1 + times_i(l0); }
+      else        { h.h[0][c] = u0 - times_i(l1); h.h[1][c] = u1 - times_i(l0); }
+    } else if (MU == 1) {
+      if (PM < 0) { h.h[0][c] = u0 + l1; h.h[1][c] = u1 - l0; }
+      else        { h.h[0][c] = u0 - l1; h.h[1][c] = u1 + l0; }
+    } else if (MU == 2) {
+      if (PM < 0) { h.h[0][c] = u0 + times_i(l0); h.h[1][c] = u1 - times_i(l1); }
+      else        { h.h[0][c] = u0 - times_i(l0); h.h[1][c] = u1 + times_i(l1); }
+    } else {
+      if (PM < 0) { h.h[0][c] = u0 - l0; h.h[1][c] = u1 - l1; }
+      else        { h.h[0][c] = u0 + l0; h.h[1][c] = u1 + l1; }
+    }
+  }
+  // row a of U (forward) or of U^dag (backward: column a of U(n - mu), conjugated)
+  cx<df64> row[3];
+  {
+    const size_t base = ((size_t)(((FWD ? dom : nd) * 4 + MU) * 9)) << g.logvd;
+    const int site = FWD ? s : ns;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int e = FWD ? a * 3 + b : b * 3 + a;
+      const float4 v = __ldg(U.p + base + ((size_t)e << g.logvd) + site);
+      row[b] = FWD ? make_cx(df64(v.x, v.y), df64(v.z, v.w)) : make_cx(df64(v.x, v.y), -df64(v.z, v.w));
+    }
+  }
+  cx<df64> uh[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    cx<df64> t = row[0] * h.h[r][0];
+    t = cmac(t, row[1], h.h[r][1]);
+    t = cmac(t, row[2], h.h[r][2]);
+    uh[r] = sign < 0 ? -t : t;
+  }
+  // rebuild the four spins of colour a (same rules as accumulate())
+  const cx<df64> h0 = uh[0], h1 = uh[1];
+  acc[0] = acc[0] + h0;
+  acc[1] = acc[1] + h1;
+  if (MU == 0) {
+    if (PM < 0) { acc[2] = acc[2] + times_mi(h1); acc[3] = acc[3] + times_mi(h0); }
+    else        { acc[2] = acc[2] + times_i(h1);  acc[3] = acc[3] + times_i(h0); }
+  } else if (MU == 1) {
+    if (PM < 0) { acc[2] = acc[2] - h1; acc[3] = acc[3] + h0; }
+    else        { acc[2] = acc[2] + h1; acc[3] = acc[3] - h0; }
+  } else if (MU == 2) {
+    if (PM < 0) { acc[2] = acc[2] + times_mi(h0); acc[3] = acc[3] + times_i(h1); }
+    else        { acc[2] = acc[2] + times_i(h0);  acc[3] = acc[3] + times_mi(h1); }
+  } else {
+    if (PM < 0) { acc[2] = acc[2] - h0; acc[3] = acc[3] - h1; }
+    else        { acc[2] = acc[2] + h0; acc[3] = acc[3] + h1; }
+  }
+}
+
+template <int A>
+__device__ __forceinline__ void df_clover_rows(const Geom& g, const DF64Spinor& in, const CloverPtrDF64& clov, int dom,
+                                               int s, cx<df64> res[4]) {
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    cx<df64> xv[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float4 v = __ldg(in.p + in.idx(g, dom, (2 * b + j / 3) * 3 + j % 3, s));
+      xv[j] = make_cx(df64(v.x, v.y), df64(v.z, v.w));
+    }
+    CloverBlockDF64 blk;
+    clov.load_block(g, dom, s, b, blk);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i = 3 * r + A;
+      cx<df64> y = make_cx(df64(0.f), df64(0.f));
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j == i) y = cmac(y, blk.diag(i), xv[j]);
+        else if (j > i) y = cmac(y, blk.off(herm_off(i, j)), xv[j]);
+        else y = cmacc(y, blk.off(herm_off(j, i)), xv[j]);
+      }
+      res[2 * b + r] = y;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
+                                                                LinkPtr<df64> U, CloverPtrDF64 clov, df64 kappa,
+                                                                int nrhs) {
+  const int a = threadIdx.y;  // colour row
+  const int rhs = blockIdx.x % nrhs;
+  const long long gid = (blockIdx.x / nrhs) * 64LL + threadIdx.z * 32 + threadIdx.x;
+  if (gid >= g.vol) return;
+  const int dom = __ldg(g.lex2dom + (int)(gid >> g.logvd));
+  const int s = (int)(gid & (g.vd - 1));
+  const int rhs_off = rhs * g.ndom;
+  const DF64Spinor inr{in.p + ((size_t)rhs_off * 12 << g.logvd)};
+  cx<df64> acc[4];
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) acc[sp] = make_cx(df64(0.f), df64(0.f));
+  df_hop<0, true>(g, inr, U, dom, s, a, acc);
+  df_hop<0, false>(g, inr, U, dom, s, a, acc);
+  df_hop<1, true>(g, inr, U, dom, s, a, acc);
+  df_hop<1, false>(g, inr, U, dom, s, a, acc);
+  df_hop<2, true>(g, inr, U, dom, s, a, acc);
+  df_hop<2, false>(g, inr, U, dom, s, a, acc);
+  df_hop<3, true>(g, inr, U, dom, s, a, acc);
+  df_hop<3, false>(g, inr, U, dom, s, a, acc);
+  // (1 + C) x, rows (block b, spin-in-block r, colour a): index i = 3 r + a;
+  // a is warp-uniform, and a compile-time row keeps the block in registers
+  cx<df64> res[4];
+  switch (a) {
+    case 0: df_clover_rows<0>(g, inr, clov, dom, s, res); break;
+    case 1: df_clover_rows<1>(g, inr, clov, dom, s, res); break;
+    default: df_clover_rows<2>(g, inr, clov, dom, s, res); break;
+  }
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) {
+    const cx<df64> o = make_cx(fma(-kappa, acc[sp].re, res[sp].re), fma(-kappa, acc[sp].im, res[sp].im));
+    out.p[out.idx(g, dom + rhs_off, sp * 3 + a, s)] = make_float4(o.re.hi, o.re.lo, o.im.hi, o.im.lo);
+  }
 }
 
 // float64 (double2) fields -> double-float (float4) copies, elementwise
