@@ -212,99 +212,6 @@ __device__ __forceinline__ void st_inter(const Geom& g, const SIO& x, const unsi
   }
 }
 
-// Compacted surface term.  The 512 domain-leaving hops of a 4^4 domain (64
-// face sites x 8 faces) are dealt out two per thread, one face per warp, so
-// no lane idles; each hop leaves its projected product U h (12 floats) in a
-// shared slot [face][face index], and every site then gathers the slots of
-// the faces it lies on.
-// face index of site s on a face normal to MU: the other three 2-bit coordinates
-template <int MU>
-__device__ __forceinline__ int face_index(int s) {
-  const int lower = s & ((1 << (2 * MU)) - 1);
-  const int upper = s >> (2 * MU + 2);
-  return lower | (upper << (2 * MU));
-}
-template <int MU>
-__device__ __forceinline__ int face_site(int f, int c) {
-  const int lower = f & ((1 << (2 * MU)) - 1);
-  const int upper = f >> (2 * MU);
-  return lower | (c << (2 * MU)) | (upper << (2 * MU + 2));
-}
-
-// one domain-leaving hop (face = 2 MU + backward) for face index f; stores U h
-template <int MU, bool BWD, bool HALF, typename SIO>
-__device__ __forceinline__ void surface_hop(const Geom& g, const SIO& x, const void* links, int dom, int f,
-                                            int rhs_off, float4* slot) {
-  constexpr int step = 1 << (2 * MU);
-  HalfSpinor<float> h, uh;
-  Spinor<float> p;
-  if (!BWD) {
-    const int s = face_site<MU>(f, 3);
-    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU);
-    const int sign = ((__ldg(g.tflag + dom) >> (2 * MU)) & 1) ? g.bc_t : 1;
-    x.load(g, nd + rhs_off, s - 3 * step, p);
-    project<MU, -1>(p, h);
-    su3_mul(StageT<HALF>::link((const unsigned char*)links + (size_t)dom * StageT<HALF>::LINK_BYTES, MU, s), h, uh);
-    if (sign < 0) scale_half(uh, -1.0f);
-  } else {
-    const int s = face_site<MU>(f, 0);
-    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU + 1);
-    const int sign = ((__ldg(g.tflag + dom) >> (2 * MU + 1)) & 1) ? g.bc_t : 1;
-    const int ns = s + 3 * step;
-    x.load(g, nd + rhs_off, ns, p);
-    project<MU, +1>(p, h);
-    su3_dag_mul(StageT<HALF>::link((const unsigned char*)links + (size_t)nd * StageT<HALF>::LINK_BYTES, MU, ns), h,
-                uh);
-    if (sign < 0) scale_half(uh, -1.0f);
-  }
-  // slot layout [face 8][3 float4][64]: conflict-free for consecutive f
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const cx<float> a0 = uh.h[(2 * k) / 3][(2 * k) % 3];
-    const cx<float> a1 = uh.h[(2 * k + 1) / 3][(2 * k + 1) % 3];
-    slot[k * 64 + f] = make_float4(a0.re, a0.im, a1.re, a1.im);
-  }
-}
-
-template <int MU, bool BWD>
-__device__ __forceinline__ void surface_gather(const float4* slots, int s, Spinor<float>& acc) {
-  const int c = (s >> (2 * MU)) & 3;
-  if (c == (BWD ? 0 : 3)) {
-    const float4* slot = slots + (2 * MU + (BWD ? 1 : 0)) * 192;
-    const int f = face_index<MU>(s);
-    HalfSpinor<float> uh;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float4 v = slot[k * 64 + f];
-      uh.h[(2 * k) / 3][(2 * k) % 3] = make_cx(v.x, v.y);
-      uh.h[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v.z, v.w);
-    }
-    accumulate<MU, BWD ? +1 : -1>(acc, uh);
-  }
-}
-
-template <bool HALF, typename SIO>
-__device__ __forceinline__ void surface_compacted(const Geom& g, const SIO& x, const void* links, int dom, int tid,
-                                                  int rhs_off, float4* slots) {
-  const int face = tid >> 5;   // one face per warp
-  const int lane = tid & 31;
-  float4* slot = slots + face * 192;
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    const int f = lane + 32 * half;
-    switch (face) {
-      case 0: surface_hop<0, false, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-      case 1: surface_hop<0, true, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-      case 2: surface_hop<1, false, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-      case 3: surface_hop<1, true, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-      case 4: surface_hop<2, false, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-      case 5: surface_hop<2, true, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-      case 6: surface_hop<3, false, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-      default: surface_hop<3, true, HALF>(g, x, links, dom, f, rhs_off, slot); break;
-    }
-  }
-}
-
 template <bool HALF>
 __device__ __forceinline__ void st_clover(const unsigned char* sc, int s, Spinor<float>& psi) {
 #pragma unroll
@@ -350,13 +257,16 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   for (int r = 0; r < a.nrhs; ++r) {
     const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
     const int rhs_off = r * g.ndom;
-    if (r > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
     Spinor<float> src;
     a.s_in.load(g, domr, s, src);
     Spinor<float> acc;
     zero(acc);
-    // the surface hops leave their products in the (still free) x buffer
-    if (a.do_surface) surface_compacted<HALF>(g, a.x, a.links, dom, s, rhs_off, sx);
+    if (a.do_surface) {
+      st_inter<0, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
+      st_inter<1, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
+      st_inter<2, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
+      st_inter<3, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
+    }
     if (r == 0) {
       __syncthreads();  // barrier initialisation visible to every thread
       const bool ok = mbar_wait_bounded(bar, 0);
@@ -368,18 +278,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
         return;
       }
     } else {
-      __syncthreads();  // surface products visible
-    }
-    if (a.do_surface) {
-      surface_gather<0, false>(sx, s, acc);
-      surface_gather<0, true>(sx, s, acc);
-      surface_gather<1, false>(sx, s, acc);
-      surface_gather<1, true>(sx, s, acc);
-      surface_gather<2, false>(sx, s, acc);
-      surface_gather<2, true>(sx, s, acc);
-      surface_gather<3, false>(sx, s, acc);
-      surface_gather<3, true>(sx, s, acc);
-      __syncthreads();  // all products read before the x buffer is overwritten
+      __syncthreads();  // every thread is done with the previous rhs's x in shared memory
     }
     if (a.do_surface) {
       st_clover<HALF>(sc, s, acc);
