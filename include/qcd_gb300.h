@@ -65,7 +65,12 @@ enum qcd_status {
   QCD_ERR_STATE = 8           /* call out of order (no gauge field, ...)    */
 };
 
-enum qcd_precision { QCD_PREC_DOUBLE = 0, QCD_PREC_SINGLE = 1, QCD_PREC_HALF = 2 };
+enum qcd_precision {
+  QCD_PREC_DOUBLE = 0,
+  QCD_PREC_SINGLE = 1,
+  QCD_PREC_HALF = 2,
+  QCD_PREC_HALF_GAUGE = 3  /* SAP only: float16 links and C_inv, float32 vectors */
+};
 enum qcd_basis { QCD_BASIS_CHIRAL = 0, QCD_BASIS_PAPER = 1 };
 
 typedef struct qcd_ctx qcd_ctx;
@@ -79,7 +84,9 @@ typedef struct qcd_solve_params {
   int max_inner;       /* BiCGStab iterations per inner solve (Alg. 5)      */
   int n_sap;           /* loop count of Algorithm 1 (K applied n_sap+1 times) */
   int n_jac;           /* A_EE applications in Algorithm 2 (>= 1)            */
-  int sap_prec;        /* QCD_PREC_SINGLE or QCD_PREC_HALF storage for SAP   */
+  int sap_prec;        /* SAP storage: QCD_PREC_SINGLE, QCD_PREC_HALF (links,
+                          C_inv and vectors) or QCD_PREC_HALF_GAUGE (links
+                          and C_inv only)                                    */
   int use_graph;       /* 1: replay each BiCGStab iteration as a CUDA graph  */
   int x_is_guess;      /* 1: x holds an initial guess on entry (resume)      */
   int residual_prec;   /* precision of x, r = b - D x and D in Algorithm 4:
@@ -173,8 +180,9 @@ int qcd_apply_clover(qcd_ctx* ctx, void* out, const void* in, int prec, int inve
 int qcd_apply_A_block(qcd_ctx* ctx, void* out, const void* in, int row, int col, void* stream);
 
 /* x = M_SAP b (with_A = 0, Algorithm 1) or x = A M_SAP b (with_A = 1,
- * Algorithm 3) on float32 internal fields; the sweeps store their vectors
- * in float32 (sap_prec = QCD_PREC_SINGLE) or float16 (QCD_PREC_HALF).
+ * Algorithm 3) on float32 internal fields; sap_prec = QCD_PREC_SINGLE keeps
+ * everything in float32, QCD_PREC_HALF stores links, C_inv and the sweep
+ * vectors in float16, QCD_PREC_HALF_GAUGE only links and C_inv.
  * n_sap >= 0 is the loop count of Algorithm 1; n_jac >= 1 the number of
  * A_EE applications of Algorithm 2.  out and in must not alias. */
 int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac, int sap_prec,

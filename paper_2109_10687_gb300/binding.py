@@ -24,7 +24,7 @@ QCD_ERR_NONFINITE = 6
 QCD_ERR_TIMEOUT = 7
 QCD_ERR_STATE = 8
 
-PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
+PREC_DOUBLE, PREC_SINGLE, PREC_HALF, PREC_HALF_GAUGE = 0, 1, 2, 3
 BASIS_CHIRAL, BASIS_PAPER = 0, 1
 KC_DSLASH, KC_SAP_BLOCK, KC_BLAS, KC_DOUBLE, KC_OTHER = range(5)
 

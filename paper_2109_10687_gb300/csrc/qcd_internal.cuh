@@ -664,6 +664,8 @@ void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F3
                              int n_sap, int n_jac, cudaStream_t st);
 void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int nrhs,
                              int n_sap, int n_jac, cudaStream_t st);
+void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
+                              int n_sap, int n_jac, cudaStream_t st);
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                       void* ws_s, void* ws_x16, void* ws_b16, cudaStream_t st);
 void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
@@ -671,7 +673,7 @@ void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
 // dslash modes
 enum { MODE_D = 0, MODE_DDAG = 1, MODE_A = 2 };
 // internal precision code of the double-float operator (not part of the ABI)
-constexpr int PREC_DF64 = 3;
+constexpr int PREC_DF64 = 7;
 void build_df64_copies(qcd_ctx* ctx, bool links, bool clover, cudaStream_t st);
 
 // one lattice of a ragged batch (device copy, rebuilt for every batched call)

@@ -272,6 +272,20 @@ void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_
   const bool staged = sap_staged_available(ctx) && !ctx->force_generic_sap;
   const size_t v = (size_t)g.vol;
   const size_t v4 = v * 6;
+  if (sap_prec == QCD_PREC_HALF_GAUGE) {
+    // float16 links and C_inv, float32 vectors
+    if (staged) {
+      F32Spinor xs{x}, bs{(float4*)b}, ss{(float4*)ws_s};
+      sap_staged_sequence_h16g(ctx, bs, ss, xs, bs, nrhs, n_sap, n_jac, st);
+    } else {
+      for (int r = 0; r < nrhs; ++r) {
+        F32Spinor xs{x + r * v4}, bs{(float4*)b + r * v4}, ss{(float4*)ws_s + r * v4};
+        sap_sequence<F32Spinor, LinkPtrHalf, CloverPtrF16, CloverBlockF32>(
+            ctx, bs, ss, xs, bs, LinkPtrHalf{ctx->u16}, CloverPtrF16{ctx->cinv16}, n_sap, n_jac, st);
+      }
+    }
+    return;
+  }
   if (sap_prec == QCD_PREC_SINGLE) {
     if (staged) {
       F32Spinor xs{x}, bs{(float4*)b}, ss{(float4*)ws_s};

@@ -85,12 +85,12 @@ struct StageT<false> {
   }
 };
 
-template <bool HALF>
+template <bool HALF, typename SIO>
 struct StagedArgs {
   Geom g;
   int colour, n_jac, do_surface, do_update, nrhs;
   float kappa;
-  typename StageT<HALF>::SIO s_in, s_out, x;
+  SIO s_in, s_out, x;   // vectors: float16 or float32 storage, independent of HALF
   F32Spinor b;
   const unsigned char* links;  // staging layout, all domains
   const unsigned char* clov;
@@ -236,8 +236,9 @@ __device__ __forceinline__ void st_store_x(float4* sx, int s, const Spinor<float
   }
 }
 
-template <bool HALF>
-__global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF> a) {
+// HALF: float16 links and C_inv (two CTAs per SM); SIO: storage of s and x
+template <bool HALF, typename SIO>
+__global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF, SIO> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   using ST = StageT<HALF>;
   float4* sx = reinterpret_cast<float4*>(smem);                              // 24 KB
@@ -384,10 +385,14 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_link32, nd * StageT<false>::LINK_BYTES));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov16, nd * StageT<true>::CLOV_BYTES));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov32, nd * StageT<false>::CLOV_BYTES));
-    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        6 * 256 * 16 + StageT<true>::LINK_BYTES + StageT<true>::CLOV_BYTES + 16));
-    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        6 * 256 * 16 + StageT<false>::LINK_BYTES + StageT<false>::CLOV_BYTES + 16));
+    const int s16 = 6 * 256 * 16 + StageT<true>::LINK_BYTES + StageT<true>::CLOV_BYTES + 16;
+    const int s32 = 6 * 256 * 16 + StageT<false>::LINK_BYTES + StageT<false>::CLOV_BYTES + 16;
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F16Spinor>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F32Spinor>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<false, F32Spinor>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
   }
   LaunchScope ls(ctx, QCD_KC_OTHER, st);
   build_link_stage_kernel<<<grid_for(g.vol * 4, 256), 256, 0, st>>>(g, ctx->u64, (__half2*)ctx->st_link16,
@@ -397,11 +402,10 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
   check_launch();
 }
 
-template <bool HALF>
-static void staged_sequence(qcd_ctx* ctx, typename StageT<HALF>::SIO s_first_in, typename StageT<HALF>::SIO s,
-                            typename StageT<HALF>::SIO x, F32Spinor b, int nrhs, int n_sap, int n_jac,
+template <bool HALF, typename SIO>
+static void staged_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spinor b, int nrhs, int n_sap, int n_jac,
                             cudaStream_t st) {
-  StagedArgs<HALF> a;
+  StagedArgs<HALF, SIO> a;
   a.g = ctx->geom;
   a.nrhs = nrhs;
   a.n_jac = n_jac;
@@ -420,7 +424,7 @@ static void staged_sequence(qcd_ctx* ctx, typename StageT<HALF>::SIO s_first_in,
       a.colour = colour;
       a.do_surface = (sweep == 0 && colour == 0) ? 0 : 1;
       LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
-      sap_staged_kernel<HALF><<<ctx->geom.nhalf, ST_THREADS, smem, st>>>(a);
+      sap_staged_kernel<HALF, SIO><<<ctx->geom.nhalf, ST_THREADS, smem, st>>>(a);
       check_launch();
     }
   }
@@ -428,11 +432,15 @@ static void staged_sequence(qcd_ctx* ctx, typename StageT<HALF>::SIO s_first_in,
 
 void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
                              int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<false>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
+  staged_sequence<false, F32Spinor>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
 }
 void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int nrhs,
                              int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<true>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
+  staged_sequence<true, F16Spinor>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
+}
+void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
+                              int n_sap, int n_jac, cudaStream_t st) {
+  staged_sequence<true, F32Spinor>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
 }
 
 }  // namespace qcd

@@ -719,8 +719,8 @@ extern "C" int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap,
   require_operator(ctx);
   QCD_REQUIRE(out && in && out != in, QCD_ERR_ARG, "qcd_sap_apply: bad buffers");
   QCD_REQUIRE(n_sap >= 0 && n_jac >= 1, QCD_ERR_ARG, "qcd_sap_apply: n_sap >= 0 and n_jac >= 1");
-  QCD_REQUIRE(sap_prec == QCD_PREC_SINGLE || sap_prec == QCD_PREC_HALF, QCD_ERR_ARG,
-              "qcd_sap_apply: sap_prec must be SINGLE or HALF");
+  QCD_REQUIRE(sap_prec == QCD_PREC_SINGLE || sap_prec == QCD_PREC_HALF || sap_prec == QCD_PREC_HALF_GAUGE,
+              QCD_ERR_ARG, "qcd_sap_apply: sap_prec must be SINGLE, HALF or HALF_GAUGE");
   cudaStream_t st = (cudaStream_t)stream;
   Workspace* w = workspace(ctx, 1, true);
   if (with_A) {
@@ -824,8 +824,8 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   else qcd_solve_params_default(&P);
   QCD_REQUIRE(P.tol > 0 && P.inner_tol > 0 && P.max_outer >= 1 && P.max_inner >= 1 && P.n_sap >= 0 && P.n_jac >= 1,
               QCD_ERR_ARG, "qcd_solve: bad parameters");
-  QCD_REQUIRE(P.sap_prec == QCD_PREC_SINGLE || P.sap_prec == QCD_PREC_HALF, QCD_ERR_ARG,
-              "qcd_solve: sap_prec must be SINGLE or HALF");
+  QCD_REQUIRE(P.sap_prec == QCD_PREC_SINGLE || P.sap_prec == QCD_PREC_HALF || P.sap_prec == QCD_PREC_HALF_GAUGE,
+              QCD_ERR_ARG, "qcd_solve: sap_prec must be SINGLE, HALF or HALF_GAUGE");
   cudaStream_t st = (cudaStream_t)stream;
   if (P.use_graph) {
     // stream capture is not possible on the legacy default stream: run the

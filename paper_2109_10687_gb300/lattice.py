@@ -11,8 +11,9 @@ import torch
 
 from . import binding as B
 
-PREC = {"double": B.PREC_DOUBLE, "single": B.PREC_SINGLE, "half": B.PREC_HALF,
-        B.PREC_DOUBLE: B.PREC_DOUBLE, B.PREC_SINGLE: B.PREC_SINGLE, B.PREC_HALF: B.PREC_HALF}
+PREC = {"double": B.PREC_DOUBLE, "single": B.PREC_SINGLE, "half": B.PREC_HALF, "half_gauge": B.PREC_HALF_GAUGE,
+        B.PREC_DOUBLE: B.PREC_DOUBLE, B.PREC_SINGLE: B.PREC_SINGLE, B.PREC_HALF: B.PREC_HALF,
+        B.PREC_HALF_GAUGE: B.PREC_HALF_GAUGE}
 
 
 def _canonical_real(t, device):

@@ -49,6 +49,15 @@ def test_msap_float16_storage(prob):
     assert rel_l2(got, ref) <= 5e-3
 
 
+def test_msap_float16_gauge_storage(prob):
+    """float16 links and C_inv with float32 vectors: an approximation of M_SAP
+    at the level of half-precision rounding of the operator."""
+    b = prob.source(2105)
+    got = to_np(prob.lat.sap(b, 4, 4, "half_gauge"))
+    ref = sap.msap(prob.op, b, 4, 4)
+    assert rel_l2(got, ref) <= 5e-3
+
+
 def test_sap_reduces_residual(prob):
     """A M_SAP is close to the identity: |b - A M b| / |b| well below 1."""
     b = prob.source(2104)

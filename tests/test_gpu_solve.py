@@ -33,7 +33,7 @@ def c1_ref(c1):
     return b, x
 
 
-@pytest.mark.parametrize("sap_prec", ["single", "half"])
+@pytest.mark.parametrize("sap_prec", ["single", "half", "half_gauge"])
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_solve_to_1e10(c1, c1_ref, sap_prec, use_graph):
     b, x_ref = c1_ref
