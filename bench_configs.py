@@ -3,8 +3,9 @@
 c1        8^4, eps 0.3, kappa 0.12, c_sw 1.0: float32 SAP-BiCGStab to relative
           residual 1e-6 (the small solve).
 c3        48^4, eps 0.25, kappa 0.125, c_sw 1.1: the 12 spin-colour point
-          sources at the origin solved together (float16 SAP + float32
-          BiCGStab + float64 correction to 1e-10, graph-replayed iterations)
+          sources at the origin solved together (SAP with float16 links and
+          C_inv + float32 BiCGStab + float64 correction to 1e-10, the inner
+          loop one CUDA graph with a conditional while node)
           against 12 sequential plain float32 solves.
 c4        16^4, eps 0.3, kappa 0.12, c_sw 1.0: gradients of Re(eta^dag D^-1 b)
           with respect to b and U (two solves + force kernels).
@@ -35,12 +36,12 @@ def _lat(dims, eps, kappa, csw, seed, domain=(4, 4, 4, 4)):
     return lat
 
 
-def _params(sap_prec="half", tol=1e-10, graph=1):
+def _params(sap_prec="half_gauge", tol=1e-10, graph=2):
     from paper_2109_10687_gb300 import binding as B
     p = B.qcd_solve_params_default()
     p.tol = tol
-    p.sap_prec = B.PREC_HALF if sap_prec == "half" else B.PREC_SINGLE
-    p.inner_tol = 1e-5 if sap_prec == "half" else 1e-6
+    p.sap_prec = {"half": B.PREC_HALF, "half_gauge": B.PREC_HALF_GAUGE, "single": B.PREC_SINGLE}[sap_prec]
+    p.inner_tol = 1e-5
     p.max_inner = 2000
     p.use_graph = graph
     return p
@@ -85,8 +86,8 @@ def c1(args):
     b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2001))).cuda().contiguous()
     x = torch.zeros_like(b)
     res = {}
-    for name, p in (("plain_f32", _params("single", 1e-6, 0)), ("plain_f32_graph", _params("single", 1e-6, 1)),
-                    ("mixed_f16_graph", _params("half", 1e-6, 1))):
+    for name, p in (("plain_f32", _params("single", 1e-6, 0)), ("plain_f32_graph_loop", _params("single", 1e-6, 2)),
+                    ("mixed_f16_gauge_graph_loop", _params("half_gauge", 1e-6, 2))):
         for _ in range(3):
             B.qcd_solve(lat.ctx, x, b, 1, p)
         t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, p), max(3, args.steps))
@@ -109,8 +110,8 @@ def c3(args):
     clk = ClockSampler("0")
     clk.start()
     # warm (allocations, tuning) then time the batched mixed solve
-    B.qcd_solve(lat.ctx, x, b, 12, _params("half"))
-    t_batch, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 12, _params("half")), 1)
+    B.qcd_solve(lat.ctx, x, b, 12, _params("half_gauge"))
+    t_batch, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 12, _params("half_gauge")), 1)
     out["batched_mixed"] = {"s": t_batch, "inner": info.inner_iters, "outer": info.outer_iters,
                             "true_resid": info.true_resid, "status": rc}
     # 12 sequential plain float32 solves of the same sources
@@ -130,8 +131,9 @@ def c3(args):
     out["speedup"] = t_seq / t_batch
     out["clocks"] = clk.stop()
     return {"config": {"workload": "48^4, eps 0.25, kappa 0.125, c_sw 1.1, 12 spin-colour point sources at the "
-                                   "origin; batched float16-SAP + float32 BiCGStab + float64 correction to 1e-10 "
-                                   "(graph-replayed iterations) vs 12 sequential plain float32 solves"},
+                                   "origin; batched SAP with float16 links/C_inv + float32 BiCGStab + float64 "
+                                   "correction to 1e-10 (device-side graph loop) vs 12 sequential plain float32 "
+                                   "solves"},
             "metric": "time to FP64 residual 1e-10 for 12 right-hand sides", "unit": "s", "results": out}
 
 
@@ -144,7 +146,7 @@ def c4(args):
     b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 3002))).cuda().contiguous()
     gb = torch.zeros_like(b)
     gu = torch.zeros(lat.site_shape + (4, 3, 3, 2), dtype=torch.float64, device="cuda")
-    p = _params("half")
+    p = _params("half_gauge")
     B.qcd_grad(lat.ctx, eta, b, gb, gu, project=1, params=p)
     t, _ = _timed(lambda: B.qcd_grad(lat.ctx, eta, b, gb, gu, project=1, params=p), max(3, args.steps))
     return {"config": {"workload": "16^4, eps 0.3, kappa 0.12, c_sw 1.0: gradients of Re(eta^dag D^-1 b) wrt b and "
@@ -162,8 +164,8 @@ def c5(args):
     clk.start()
     d = _dslash_gbs(lat, b)
     x = torch.zeros_like(b)
-    B.qcd_solve(lat.ctx, x, b, 1, _params("half"))
-    t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, _params("half")), 2)
+    B.qcd_solve(lat.ctx, x, b, 1, _params("half_gauge"))
+    t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, _params("half_gauge")), 2)
     tf, (rcf, infof) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, _params("single")), 1)
     return {"config": {"workload": "64^4, eps 0.2, kappa 0.126, c_sw 1.1, one Gaussian source"},
             "metric": "Dslash GB/s; time to FP64 residual 1e-10", "unit": "GB/s; s",
@@ -205,8 +207,8 @@ def c5ragged(args):
     total = sum(vols)
     gbs = D_BYTES_PER_SITE * total / (ms * 1e-3) / 1e9
     xs = [torch.zeros_like(b) for b in bs]
-    B.qcd_batch_solve(bt, xs, bs, _params("half"))
-    t, (rc, infos) = _timed(lambda: B.qcd_batch_solve(bt, xs, bs, _params("half")), 1)
+    B.qcd_batch_solve(bt, xs, bs, _params("half_gauge"))
+    t, (rc, infos) = _timed(lambda: B.qcd_batch_solve(bt, xs, bs, _params("half_gauge")), 1)
     B.qcd_batch_destroy(bt)
     return {"config": {"workload": "ragged batch of 32 lattices, extents from {8, 16} per direction, eps 0.3, "
                                    "kappa ~ U[0.115, 0.125], c_sw 1.0, seeds 5000 + i", "sites": total},

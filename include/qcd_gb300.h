@@ -87,7 +87,10 @@ typedef struct qcd_solve_params {
   int sap_prec;        /* SAP storage: QCD_PREC_SINGLE, QCD_PREC_HALF (links,
                           C_inv and vectors) or QCD_PREC_HALF_GAUGE (links
                           and C_inv only)                                    */
-  int use_graph;       /* 1: replay each BiCGStab iteration as a CUDA graph  */
+  int use_graph;       /* 0: kernels launched one by one; 1: each half of a
+                          BiCGStab iteration replayed as a CUDA graph; 2: the
+                          whole inner loop as one graph with a conditional
+                          while node (no host round trip per iteration)      */
   int x_is_guess;      /* 1: x holds an initial guess on entry (resume)      */
   int residual_prec;   /* precision of x, r = b - D x and D in Algorithm 4:
                           1 native float64 (default), 0 double-float (two

@@ -342,6 +342,7 @@ extern "C" int qcd_create(const int dims[4], const int domain[4], int bc_t, int 
     g.nbr = ctx->d_nbr;
     g.tflag = ctx->d_tflag;
     g.lex2dom = ctx->d_lex2dom;
+    g.run_flag = nullptr;
     ctx->prof = new Profiler();
   } catch (const qcd::Error& e) {
     g_create_error = e.msg;

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                   typename Prec<R>::CP clov, R kappa, int nrhs) {
   const int rhs = blockIdx.x % nrhs;
   const long long gid = (blockIdx.x / nrhs) * (long long)THREADS + threadIdx.x;
-  if (gid >= g.vol) return;
+  if (gid >= g.vol || loop_idle(g)) return;
   dslash_site<R, MODE>(g, out, in, U, clov, kappa, gid, rhs);
 }
 

@@ -58,7 +58,14 @@ struct Geom {
   const int* nbr;  // [ndom][8]: neighbour domain across face 2 mu (+) / 2 mu + 1 (-)
   const unsigned char* tflag;  // [ndom]: bit k set when face k crosses t = Lt-1 <-> 0
   const int* lex2dom;          // [ndom]: lexicographic domain index -> storage index
+  const int* run_flag;         // if set: operator kernels return at once when *run_flag == 0
 };
+
+// true when a kernel launched inside the device-side solver loop has nothing
+// left to do (every right-hand side has stopped iterating)
+__device__ __forceinline__ bool loop_idle(const Geom& g) {
+  return g.run_flag != nullptr && *(volatile const int*)g.run_flag == 0;
+}
 
 // Neighbouring site of (dom, s) in direction mu, forward (fwd) or backward.
 // Returns the sign of the boundary condition carried by the hop.

@@ -130,6 +130,7 @@ template <typename SIO, typename LP, typename CP, typename CB>
 __global__ void __launch_bounds__(SAP_THREADS) sap_block_kernel(SapArgs<SIO, LP, CP> a) {
   __shared__ float4 sx[6 * SAP_THREADS];
   const Geom& g = a.g;
+  if (loop_idle(g)) return;
   const int t = threadIdx.x;
   const int per_cta = SAP_THREADS >> g.logvd;           // domains per CTA
   const int local = t >> g.logvd;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(SAP_THREADS) sap_block_kernel(SapArgs<SIO, LP,
 // blockIdx.y selects the right-hand side)
 __global__ void f32_to_f16_kernel(Geom g, F16Spinor out, F32Spinor in) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= g.vol) return;
+  if (gid >= g.vol || loop_idle(g)) return;
   const int dom = (int)(gid >> g.logvd) + blockIdx.y * g.ndom, s = (int)(gid & (g.vd - 1));
   Spinor<float> a;
   in.load(g, dom, s, a);
@@ -218,7 +219,7 @@ __global__ void f32_to_f16_kernel(Geom g, F16Spinor out, F32Spinor in) {
 }
 __global__ void f16_to_f32_kernel(Geom g, F32Spinor out, F16Spinor in) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= g.vol) return;
+  if (gid >= g.vol || loop_idle(g)) return;
   const int dom = (int)(gid >> g.logvd) + blockIdx.y * g.ndom, s = (int)(gid & (g.vd - 1));
   Spinor<float> a;
   in.load(g, dom, s, a);

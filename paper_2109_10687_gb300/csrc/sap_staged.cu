@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   unsigned char* sc = sl + ST::LINK_BYTES;                                     // C_inv
   uint64_t* bar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);
   const Geom& g = a.g;
+  if (loop_idle(g)) return;
   const int s = threadIdx.x;
   const int dom = a.colour * g.nhalf + blockIdx.x;
 

@@ -55,7 +55,23 @@ struct Workspace {
   Scal* scal = nullptr;
   Scal* h_scal = nullptr;  // pinned
   double* h_red = nullptr; // pinned
+  int* ctrl = nullptr;     // device: [0] rhs still iterating, [1] iterations, [2] iteration limit
+  int* h_ctrl = nullptr;   // pinned
   int nblocks = 0;
+  // instantiated CUDA graphs of the inner loop, reused while the key matches
+  struct Graphs {
+    int nrhs = -1, n_sap = -1, n_jac = -1, sap_prec = -1, mode = -1;
+    double kappa = 0.0;
+    cudaGraphExec_t half1 = nullptr, half2 = nullptr, loop = nullptr;
+    long long n1 = 0, n2 = 0, nloop = 0;  // kernels per replay
+    void reset() {
+      if (half1) cudaGraphExecDestroy(half1);
+      if (half2) cudaGraphExecDestroy(half2);
+      if (loop) cudaGraphExecDestroy(loop);
+      half1 = half2 = loop = nullptr;
+      nrhs = -1;
+    }
+  } graphs;
 };
 
 void workspace_free(qcd_ctx* ctx) {
@@ -67,6 +83,9 @@ void workspace_free(qcd_ctx* ctx) {
     if (p) cudaFree(p);
   if (w->h_scal) cudaFreeHost(w->h_scal);
   if (w->h_red) cudaFreeHost(w->h_red);
+  if (w->ctrl) cudaFree(w->ctrl);
+  if (w->h_ctrl) cudaFreeHost(w->h_ctrl);
+  w->graphs.reset();
   delete w;
   ctx->ws = nullptr;
 }
@@ -100,6 +119,9 @@ static Workspace* workspace(qcd_ctx* ctx, int nrhs, bool solver) {
   QCD_CUDA_CHECK(cudaMemset(w->scal, 0, sizeof(Scal) * keep_nrhs));
   QCD_CUDA_CHECK(cudaMallocHost(&w->h_scal, sizeof(Scal) * keep_nrhs));
   QCD_CUDA_CHECK(cudaMallocHost(&w->h_red, sizeof(double) * MAX_RED_OUT * keep_nrhs));
+  QCD_CUDA_CHECK(cudaMalloc(&w->ctrl, sizeof(int) * 4));
+  QCD_CUDA_CHECK(cudaMemset(w->ctrl, 0, sizeof(int) * 4));
+  QCD_CUDA_CHECK(cudaMallocHost(&w->h_ctrl, sizeof(int) * 4));
   if (want_solver) {
     const size_t b32 = w->v4 * sizeof(float4) * keep_nrhs;
     float4** vecs[] = {&w->x, &w->r, &w->p, &w->q, &w->t, &w->zp, &w->zr, &w->rt, &w->tmp32};
@@ -228,7 +250,7 @@ __global__ void k_cdot(const float4* __restrict__ a, const float4* __restrict__ 
 
 // BiCGStab initialisation: x = 0, r = p = rt = b, bnorm2 = |b|^2, rho_0 = bnorm2
 __global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float4* p, float4* rt, size_t n4,
-                       double tol2, Scal* scal, double* partials, unsigned* counters) {
+                       double tol2, Scal* scal, double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   float s = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
@@ -253,12 +275,13 @@ __global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float
       sc.status = QCD_ERR_NONFINITE;
       sc.done = 1;
     }
+    if (!sc.done) atomicAdd(ctrl, 1);  // one more right-hand side iterating
   }
 }
 
 // alpha = rho_0 / <rt|q>
 __global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict__ q, size_t n4, Scal* scal,
-                        double* partials, unsigned* counters) {
+                        double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
   float re = 0.f, im = 0.f;
@@ -270,6 +293,7 @@ __global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict_
     if (!(dn > 0.0) || !isfinite(dn)) {
       sc.status = isfinite(dn) ? QCD_ERR_BREAKDOWN : QCD_ERR_NONFINITE;
       sc.done = 1;
+      atomicSub(ctrl, 1);
     } else {
       sc.alpha_re = (sc.rho0_re * tot[0] + sc.rho0_im * tot[1]) / dn;
       sc.alpha_im = (sc.rho0_im * tot[0] - sc.rho0_re * tot[1]) / dn;
@@ -279,7 +303,7 @@ __global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict_
 
 // x += alpha z; r -= alpha q; rnorm2 = |r|^2; first exit test
 __global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ q, size_t n4,
-                          Scal* scal, double* partials, unsigned* counters) {
+                          Scal* scal, double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
   const float ar = (float)sc.alpha_re, ai = (float)sc.alpha_im;
@@ -296,16 +320,18 @@ __global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, co
     if (!isfinite(tot[0])) {
       sc.status = QCD_ERR_NONFINITE;
       sc.done = 1;
+      atomicSub(ctrl, 1);
     } else if (tot[0] < sc.tol2 * sc.bnorm2) {
       sc.conv = 1;
       sc.done = 1;
+      atomicSub(ctrl, 1);
     }
   }
 }
 
 // omega = <t|r> / |t|^2
 __global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__ r, size_t n4, Scal* scal,
-                        double* partials, unsigned* counters) {
+                        double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
   float re = 0.f, im = 0.f, tt = 0.f;
@@ -319,6 +345,7 @@ __global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__
     if (!(tot[2] > 0.0) || !isfinite(tot[2])) {
       sc.status = isfinite(tot[2]) ? QCD_ERR_BREAKDOWN : QCD_ERR_NONFINITE;
       sc.done = 1;
+      atomicSub(ctrl, 1);
     } else {
       sc.omega_re = tot[0] / tot[2];
       sc.omega_im = tot[1] / tot[2];
@@ -329,7 +356,7 @@ __global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__
 // x += omega z; r -= omega t; rnorm2 = |r|^2, rho = <rt|r>; second exit test;
 // beta = alpha rho / (rho_0 omega); rho_0 = rho
 __global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ t,
-                          const float4* __restrict__ rt, size_t n4, Scal* scal, double* partials, unsigned* counters) {
+                          const float4* __restrict__ rt, size_t n4, Scal* scal, double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
   const float wr = (float)sc.omega_re, wi = (float)sc.omega_im;
@@ -347,9 +374,11 @@ __global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, co
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
       sc.status = QCD_ERR_NONFINITE;
       sc.done = 1;
+      atomicSub(ctrl, 1);
     } else if (tot[0] < sc.tol2 * sc.bnorm2) {
       sc.conv = 1;
       sc.done = 1;
+      atomicSub(ctrl, 1);
     } else {
       // beta = (alpha rho) / (rho_0 omega)
       const double nr = sc.alpha_re * tot[1] - sc.alpha_im * tot[2];
@@ -360,6 +389,7 @@ __global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, co
       if (!(dn > 0.0) || (tot[1] == 0.0 && tot[2] == 0.0)) {
         sc.status = QCD_ERR_BREAKDOWN;
         sc.done = 1;
+      atomicSub(ctrl, 1);
       } else {
         sc.beta_re = (nr * dr + ni * di) / dn;
         sc.beta_im = (ni * dr - nr * di) / dn;
@@ -529,6 +559,13 @@ __global__ void k_df_axpy_f32(Geom g, float4* x, const float4* __restrict__ q, c
   }
 }
 
+// Condition of the device-side inner loop: one more iteration while some
+// right-hand side iterates and the limit is not reached.
+__global__ void k_loop_cond(cudaGraphConditionalHandle handle, int* ctrl) {
+  const int it = ++ctrl[1];
+  cudaGraphSetConditional(handle, (ctrl[0] > 0 && it < ctrl[2]) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -559,8 +596,9 @@ static void bicg_half1(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_par
   const dim3 grid(w->nblocks, nrhs);
   am_sap(ctx, w, w->zp, w->q, w->p, nrhs, P.n_sap, P.n_jac, P.sap_prec, st);
   LaunchScope ls(ctx, QCD_KC_BLAS, st);
-  k_alpha<<<grid, RED_THREADS, 0, st>>>(w->rt, w->q, w->v4, w->scal, w->partials, w->counters);
-  k_update1<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zp, w->q, w->v4, w->scal, w->partials, w->counters);
+  k_alpha<<<grid, RED_THREADS, 0, st>>>(w->rt, w->q, w->v4, w->scal, w->partials, w->counters, w->ctrl);
+  k_update1<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zp, w->q, w->v4, w->scal, w->partials, w->counters,
+                                         w->ctrl);
   ctx->launches++;
   check_launch();
 }
@@ -568,8 +606,9 @@ static void bicg_half2(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_par
   const dim3 grid(w->nblocks, nrhs);
   am_sap(ctx, w, w->zr, w->t, w->r, nrhs, P.n_sap, P.n_jac, P.sap_prec, st);
   LaunchScope ls(ctx, QCD_KC_BLAS, st);
-  k_omega<<<grid, RED_THREADS, 0, st>>>(w->t, w->r, w->v4, w->scal, w->partials, w->counters);
-  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zr, w->t, w->rt, w->v4, w->scal, w->partials, w->counters);
+  k_omega<<<grid, RED_THREADS, 0, st>>>(w->t, w->r, w->v4, w->scal, w->partials, w->counters, w->ctrl);
+  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zr, w->t, w->rt, w->v4, w->scal, w->partials, w->counters,
+                                         w->ctrl);
   k_update_p<<<grid, RED_THREADS, 0, st>>>(w->p, w->r, w->q, w->v4, w->scal);
   ctx->launches += 2;
   check_launch();
@@ -577,63 +616,118 @@ static void bicg_half2(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_par
 
 // Algorithm 5 on A M_SAP z = b32 (float32 internal fields, nrhs stacked);
 // solution accumulated in w->x.  Returns iterations; fills per-rhs status.
+//   use_graph 0: kernels launched one by one, the host reads the exit flags
+//                after each half-iteration;
+//   use_graph 1: each half-iteration replayed as a CUDA graph, same host checks;
+//   use_graph 2: the whole loop is one CUDA graph with a conditional WHILE
+//                node: a one-thread kernel sets the condition from the count
+//                of right-hand sides still iterating, and every operator
+//                kernel of an iteration returns at once when that count is
+//                zero, so the host waits only for the finished loop.
+// Graphs are cached in the workspace and reused while nrhs, n_sap, n_jac,
+// sap_prec and kappa are unchanged.
 static int bicgstab_sap(qcd_ctx* ctx, Workspace* w, const float4* b32, int nrhs, const qcd_solve_params& P,
                         cudaStream_t st, int* worst_status) {
   const dim3 grid(w->nblocks, nrhs);
+  w->h_ctrl[0] = 0;
+  w->h_ctrl[1] = 0;
+  w->h_ctrl[2] = P.max_inner;
+  QCD_CUDA_CHECK(cudaMemcpyAsync(w->ctrl, w->h_ctrl, sizeof(int) * 3, cudaMemcpyHostToDevice, st));
   {
     LaunchScope ls(ctx, QCD_KC_BLAS, st);
     k_init<<<grid, RED_THREADS, 0, st>>>(b32, w->x, w->r, w->p, w->rt, w->v4, P.inner_tol * P.inner_tol, w->scal,
-                                         w->partials, w->counters);
+                                         w->partials, w->counters, w->ctrl);
     check_launch();
   }
-  int it = 0;
-  cudaGraphExec_t g1 = nullptr, g2 = nullptr;
-  long long n1 = 0, n2 = 0;  // kernels per captured half-iteration
-  if (P.use_graph) {
-    // capture each half-iteration once and replay it; the launch counter
-    // advances by the kernels of a graph on every replay
+  const int mode = P.use_graph < 0 ? 0 : (P.use_graph > 2 ? 2 : P.use_graph);
+  Workspace::Graphs& G = w->graphs;
+  if (mode > 0 && (G.nrhs != nrhs || G.n_sap != P.n_sap || G.n_jac != P.n_jac || G.sap_prec != P.sap_prec ||
+                   G.mode != mode || G.kappa != ctx->kappa)) {
+    G.reset();
     cudaGraph_t gr;
-    long long c0 = ctx->launches;
-    QCD_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    bicg_half1(ctx, w, nrhs, P, st);
-    QCD_CUDA_CHECK(cudaStreamEndCapture(st, &gr));
-    QCD_CUDA_CHECK(cudaGraphInstantiate(&g1, gr, 0));
-    cudaGraphDestroy(gr);
-    n1 = ctx->launches - c0;
-    c0 = ctx->launches;
-    QCD_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    bicg_half2(ctx, w, nrhs, P, st);
-    QCD_CUDA_CHECK(cudaStreamEndCapture(st, &gr));
-    QCD_CUDA_CHECK(cudaGraphInstantiate(&g2, gr, 0));
-    cudaGraphDestroy(gr);
-    n2 = ctx->launches - c0;
-    ctx->launches -= n1 + n2;
-  }
-  bool finished = all_done(w, nrhs, st);
-  while (!finished && it < P.max_inner) {
-    ++it;
-    if (g1) {
-      QCD_CUDA_CHECK(cudaGraphLaunch(g1, st));
-      ctx->launches += n1;
-    } else {
+    const long long c_start = ctx->launches;
+    long long c0 = c_start;
+    if (mode == 1) {
+      QCD_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       bicg_half1(ctx, w, nrhs, P, st);
-    }
-    if (all_done(w, nrhs, st)) break;
-    if (g2) {
-      QCD_CUDA_CHECK(cudaGraphLaunch(g2, st));
-      ctx->launches += n2;
-    } else {
+      QCD_CUDA_CHECK(cudaStreamEndCapture(st, &gr));
+      QCD_CUDA_CHECK(cudaGraphInstantiate(&G.half1, gr, 0));
+      cudaGraphDestroy(gr);
+      G.n1 = ctx->launches - c0;
+      c0 = ctx->launches;
+      QCD_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       bicg_half2(ctx, w, nrhs, P, st);
+      QCD_CUDA_CHECK(cudaStreamEndCapture(st, &gr));
+      QCD_CUDA_CHECK(cudaGraphInstantiate(&G.half2, gr, 0));
+      cudaGraphDestroy(gr);
+      G.n2 = ctx->launches - c0;
+    } else {
+      QCD_CUDA_CHECK(cudaGraphCreate(&gr, 0));
+      cudaGraphConditionalHandle handle;
+      QCD_CUDA_CHECK(cudaGraphConditionalHandleCreate(&handle, gr, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      QCD_CUDA_CHECK(cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      // operator kernels of the body return at once when no rhs iterates
+      ctx->geom.run_flag = w->ctrl;
+      QCD_CUDA_CHECK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      bicg_half1(ctx, w, nrhs, P, st);
+      bicg_half2(ctx, w, nrhs, P, st);
+      k_loop_cond<<<1, 1, 0, st>>>(handle, w->ctrl);
+      ctx->launches++;
+      const cudaError_t ce = cudaStreamEndCapture(st, &body);
+      ctx->geom.run_flag = nullptr;
+      QCD_CUDA_CHECK(ce);
+      QCD_CUDA_CHECK(cudaGraphInstantiate(&G.loop, gr, 0));
+      cudaGraphDestroy(gr);
+      G.nloop = ctx->launches - c0;
     }
-    finished = all_done(w, nrhs, st);
+    ctx->launches = c_start;  // captured kernels are counted when replayed
+    G.nrhs = nrhs;
+    G.n_sap = P.n_sap;
+    G.n_jac = P.n_jac;
+    G.sap_prec = P.sap_prec;
+    G.mode = mode;
+    G.kappa = ctx->kappa;
   }
-  if (g1) cudaGraphExecDestroy(g1);
-  if (g2) cudaGraphExecDestroy(g2);
+  int it = 0;
+  if (mode == 2) {
+    QCD_CUDA_CHECK(cudaGraphLaunch(G.loop, st));
+    QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_ctrl, w->ctrl, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
+    QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(Scal) * nrhs, cudaMemcpyDeviceToHost, st));
+    QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+    it = w->h_ctrl[1];
+    ctx->launches += (long long)it * G.nloop;
+  } else {
+    bool finished = all_done(w, nrhs, st);
+    while (!finished && it < P.max_inner) {
+      ++it;
+      if (mode == 1) {
+        QCD_CUDA_CHECK(cudaGraphLaunch(G.half1, st));
+        ctx->launches += G.n1;
+      } else {
+        bicg_half1(ctx, w, nrhs, P, st);
+      }
+      if (all_done(w, nrhs, st)) break;
+      if (mode == 1) {
+        QCD_CUDA_CHECK(cudaGraphLaunch(G.half2, st));
+        ctx->launches += G.n2;
+      } else {
+        bicg_half2(ctx, w, nrhs, P, st);
+      }
+      finished = all_done(w, nrhs, st);
+    }
+  }
   int worst = QCD_OK;
   for (int r = 0; r < nrhs; ++r) {
-    const Scal& s = w->h_scal[r];
-    if (s.status != QCD_OK) worst = s.status;
-    else if (!s.conv && worst == QCD_OK) worst = QCD_ERR_NOT_CONVERGED;
+    const Scal& sc = w->h_scal[r];
+    if (sc.status != QCD_OK) worst = sc.status;
+    else if (!sc.conv && worst == QCD_OK) worst = QCD_ERR_NOT_CONVERGED;
   }
   *worst_status = worst;
   return it;

@@ -34,7 +34,7 @@ def c1_ref(c1):
 
 
 @pytest.mark.parametrize("sap_prec", ["single", "half", "half_gauge"])
-@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
 def test_solve_to_1e10(c1, c1_ref, sap_prec, use_graph):
     b, x_ref = c1_ref
     x, rc, info = c1.lat.solve(b, tol=1e-10, inner_tol=1e-6 if sap_prec == "single" else 1e-5,
@@ -79,14 +79,26 @@ def test_algorithm5_iterates_match_oracle(c1):
     assert rel_l2(to_np(x), bn * x_or) < 2e-5
 
 
-def test_batched_point_sources(c1):
-    """Several spin-colour point sources in one batched solve."""
+@pytest.mark.parametrize("use_graph", [0, 2])
+def test_batched_point_sources(c1, use_graph):
+    """Several spin-colour point sources in one batched solve (the device-side
+    graph loop runs until the last right-hand side has converged)."""
     srcs = np.stack([point_source(c1.dims, c, s) for c, s in ((0, 0), (1, 2), (2, 3))])
-    x, rc, info = c1.lat.solve(srcs, nrhs=3, tol=1e-10)
+    x, rc, info = c1.lat.solve(srcs, nrhs=3, tol=1e-10, use_graph=use_graph, sap_prec="half_gauge",
+                               inner_tol=1e-5)
     x = to_np(x)
     assert rc == 0
     for r in range(3):
         assert true_resid(c1.op, x[r], srcs[r]) < 1e-10
+
+
+def test_graph_loop_iteration_limit(c1):
+    """The device-side loop stops at max_inner and reports it."""
+    from paper_2109_10687_gb300 import binding as B
+    b = gaussian_spinor(c1.dims, 2005)
+    x, rc, info = c1.lat.solve(b, tol=1e-12, max_outer=1, max_inner=2, use_graph=2, raise_on_error=False)
+    assert rc == B.QCD_ERR_NOT_CONVERGED
+    assert info.inner_iters == 2
 
 
 def test_zero_source(c1):
