@@ -100,7 +100,7 @@ __device__ __forceinline__ void hopping(const Geom& g, const SIO& in, const LP& 
 // numbered rhs-fastest, so the nrhs blocks that share a tile of sites (and
 // its links and clover) run back to back and reuse them from L2.
 // One site (lexicographic-domain index gid) of one right-hand side.
-template <typename R, int MODE>
+template <typename R, int MODE, bool HINT = false>
 __device__ __forceinline__ void dslash_site(const Geom& g, const typename Prec<R>::SIO& out,
                                             const typename Prec<R>::SIO& in, const typename Prec<R>::LP& U,
                                             const typename Prec<R>::CP& clov, R kappa, long long gid, int rhs) {
@@ -115,7 +115,10 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const typename Prec<R
   else hopping<-1, +1, 0>(g, in, U, dom, s, rhs_off, acc);
   Spinor<R> x;
   in.load(g, dom + rhs_off, s, x);
-  if (MODE == MODE_A) {
+  if constexpr (HINT) {
+    const CloverPtrF32Stream cs{clov.p};
+    clover_mul<R, CloverPtrF32Stream, typename Prec<R>::CB>(cs, g, dom, s, MODE == MODE_A ? acc : x);
+  } else if (MODE == MODE_A) {
     clover_mul<R, typename Prec<R>::CP, typename Prec<R>::CB>(clov, g, dom, s, acc);
   } else {
     clover_mul<R, typename Prec<R>::CP, typename Prec<R>::CB>(clov, g, dom, s, x);
@@ -127,17 +130,22 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const typename Prec<R
       x.v[sp][c].re = fma(-kappa, acc.v[sp][c].re, x.v[sp][c].re);
       x.v[sp][c].im = fma(-kappa, acc.v[sp][c].im, x.v[sp][c].im);
     }
-  out.store(g, dom + rhs_off, s, x);
+  if constexpr (HINT) out.store_stream(g, dom + rhs_off, s, x);
+  else out.store(g, dom + rhs_off, s, x);
 }
 
-template <typename R, int MODE, int THREADS, int MINB>
+// HINT: the clover rows and the output, touched once per application, are
+// read and written with the streaming (evict-first) cache operators, so
+// that L2 keeps the spinor and link lines that neighbouring sites read
+// again.  float32 only.
+template <typename R, int MODE, int THREADS, int MINB, bool HINT>
 __global__ void __launch_bounds__(THREADS, MINB)
     dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in, typename Prec<R>::LP U,
                   typename Prec<R>::CP clov, R kappa, int nrhs) {
   const int rhs = blockIdx.x % nrhs;
   const long long gid = (blockIdx.x / nrhs) * (long long)THREADS + threadIdx.x;
   if (gid >= g.vol || loop_idle(g)) return;
-  dslash_site<R, MODE>(g, out, in, U, clov, kappa, gid, rhs);
+  dslash_site<R, MODE, HINT>(g, out, in, U, clov, kappa, gid, rhs);
 }
 
 // Ragged batch: one launch over several lattices of different sizes.  Block
@@ -202,13 +210,13 @@ __global__ void __launch_bounds__(128) ablock_kernel(Geom g, F32Spinor out, F32S
   out.store(g, dom, s, res);
 }
 
-template <typename R, int MODE, int THREADS, int MINB>
+template <typename R, int MODE, int THREADS, int MINB, bool HINT = false>
 static void launch_dslash_shape(const Geom& g, void* out, const void* in, const void* U, const void* clov, R kappa,
                                 int nrhs, cudaStream_t st) {
   using P = Prec<R>;
   const long long blocks = (long long)grid_for(g.vol, THREADS) * nrhs;
   QCD_REQUIRE(blocks < (1LL << 31), QCD_ERR_ARG, "lattice too large for one launch");
-  dslash_kernel<R, MODE, THREADS, MINB><<<(unsigned)blocks, THREADS, 0, st>>>(
+  dslash_kernel<R, MODE, THREADS, MINB, HINT><<<(unsigned)blocks, THREADS, 0, st>>>(
       g, typename P::SIO{(decltype(P::SIO::p))out}, typename P::SIO{(decltype(P::SIO::p))in},
       typename P::LP{(decltype(P::LP::p))U}, typename P::CP{(decltype(P::CP::p))clov}, kappa, nrhs);
 }
@@ -221,10 +229,15 @@ static void launch_dslash_f32(int variant, const Geom& g, void* out, const void*
     case 0: launch_dslash_shape<float, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st); break;
     case 1: launch_dslash_shape<float, MODE, 128, 5>(g, out, in, U, clov, kappa, nrhs, st); break;
     case 2: launch_dslash_shape<float, MODE, 128, 6>(g, out, in, U, clov, kappa, nrhs, st); break;
-    default: launch_dslash_shape<float, MODE, 256, 2>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 3: launch_dslash_shape<float, MODE, 256, 2>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 4: launch_dslash_shape<float, MODE, 128, 4, true>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 5: launch_dslash_shape<float, MODE, 128, 5, true>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 6: launch_dslash_shape<float, MODE, 128, 6, true>(g, out, in, U, clov, kappa, nrhs, st); break;
+    default: launch_dslash_shape<float, MODE, 256, 2, true>(g, out, in, U, clov, kappa, nrhs, st); break;
   }
 }
-static const char* kDslashShapes[] = {"128x4", "128x5", "128x6", "256x2"};
+static const char* kDslashShapes[] = {"128x4", "128x5", "128x6", "256x2", "128x4h", "128x5h", "128x6h", "256x2h"};
+constexpr int kNumDslashShapes = 8;
 
 void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st) {
   const Geom& g = ctx->geom;
@@ -257,7 +270,7 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
     };
     char key[64];
     std::snprintf(key, sizeof key, "dslash_f32_mode%d_nrhs%d", mode, nrhs);
-    const int v = tune_pick(ctx, key, 4, kDslashShapes, run, st);
+    const int v = tune_pick(ctx, key, kNumDslashShapes, kDslashShapes, run, st);
     LaunchScope ls(ctx, QCD_KC_DSLASH, st);
     run(v);
   } else {

@@ -330,6 +330,14 @@ struct F32Spinor {
 #pragma unroll
     for (int k = 0; k < 6; ++k) p[idx(g, dom, k, s)] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
   }
+  // store with the streaming cache operator (evict first)
+  __device__ __forceinline__ void store_stream(const Geom& g, int dom, int s, const Spinor<float>& a) const {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const cx<float> a0 = a.v[(2 * k) / 3][(2 * k) % 3], a1 = a.v[(2 * k + 1) / 3][(2 * k + 1) % 3];
+      __stcs(p + idx(g, dom, k, s), make_float4(a0.re, a0.im, a1.re, a1.im));
+    }
+  }
 };
 
 struct F64Spinor {
@@ -519,6 +527,17 @@ struct CloverPtrF32 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const float4 v = __ldg(p + (((size_t)(dom * 18 + 9 * b + k)) << g.logvd) + s);
+      blk.r[4 * k] = v.x; blk.r[4 * k + 1] = v.y; blk.r[4 * k + 2] = v.z; blk.r[4 * k + 3] = v.w;
+    }
+  }
+};
+// the same rows read with the streaming cache operator (evict first)
+struct CloverPtrF32Stream {
+  const float4* p;
+  __device__ __forceinline__ void load_block(const Geom& g, int dom, int s, int b, CloverBlockF32& blk) const {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = __ldcs(p + (((size_t)(dom * 18 + 9 * b + k)) << g.logvd) + s);
       blk.r[4 * k] = v.x; blk.r[4 * k + 1] = v.y; blk.r[4 * k + 2] = v.z; blk.r[4 * k + 3] = v.w;
     }
   }

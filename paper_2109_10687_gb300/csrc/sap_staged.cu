@@ -143,21 +143,52 @@ template <int MU>
 __device__ __forceinline__ int lc(int s) { return (s >> (2 * MU)) & 3; }
 
 // shared-memory x: float4 group k holds complex components 2k and 2k+1,
-// component c = spin * 3 + colour
+// component c = spin * 3 + colour; row k has 256 sites and one zero "ghost"
+// site that hops leaving the domain read instead of a neighbour
+constexpr int SX_STRIDE = 257;
+constexpr int SX_GHOST = 256;
+constexpr int SX_BYTES = 6 * SX_STRIDE * 16;
 __device__ __forceinline__ void st_load_x(const float4* sx, int site, Spinor<float>& p) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const float4 v = sx[k * 256 + site];
+    const float4 v = sx[k * SX_STRIDE + site];
     p.v[(2 * k) / 3][(2 * k) % 3] = make_cx(v.x, v.y);
     p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v.z, v.w);
   }
 }
 
-// acc += both intra-domain hops of direction MU (operand x from shared memory)
+// acc += both intra-domain hops of direction MU (operand x from shared memory).
+// x, y, z: a warp holds sites with every coordinate value along MU, so the
+// hops are computed for all lanes without branches; a hop that would leave
+// the domain reads the zero ghost site (and some valid link) and adds an
+// exact zero.  Straight-line code lets the compiler overlap the shared-memory
+// loads of several hops.  t: a warp has one t value, the branches are uniform.
 template <int MU, bool HALF>
 __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* sl, int s, Spinor<float>& acc) {
   constexpr int step = 1 << (2 * MU);
   const int c = lc<MU>(s);
+  if (MU < 3) {
+    {
+      Spinor<float> p;
+      st_load_x(sx, c < 3 ? s + step : SX_GHOST, p);
+      HalfSpinor<float> h, uh;
+      project<MU, -1>(p, h);
+      const SU3<float> u = StageT<HALF>::link(sl, MU, s);
+      su3_mul(u, h, uh);
+      accumulate<MU, -1>(acc, uh);
+    }
+    {
+      const int nb = c > 0 ? s - step : SX_GHOST;
+      Spinor<float> p;
+      st_load_x(sx, nb, p);
+      HalfSpinor<float> h, uh;
+      project<MU, +1>(p, h);
+      const SU3<float> u = StageT<HALF>::link(sl, MU, c > 0 ? s - step : s);
+      su3_dag_mul(u, h, uh);
+      accumulate<MU, +1>(acc, uh);
+    }
+    return;
+  }
   if (c < 3) {
     Spinor<float> p;
     st_load_x(sx, s + step, p);
@@ -178,38 +209,98 @@ __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* 
   }
 }
 
-// acc += both domain-leaving hops of direction MU (operand x and links from memory)
+// Surface term as face tasks.  The hops that leave a 4^4 domain start on its
+// eight faces (direction MU, side 0: sites with c_MU = 3, forward hop; side 1:
+// c_MU = 0, backward hop), 64 sites each, 512 per domain.  Thread tau takes
+// task tau (directions 0, 1) and task tau + 256 (directions 2, 3); a warp's
+// 32 tasks share direction and side, so no lane idles (with one thread per
+// site, each face hop is a branch that a quarter of the lanes take).  The
+// hop result U P x (a half spinor) goes to a slot in shared memory; the
+// site's thread adds the slots of its faces afterwards.
+// Slots: float4 [MU 4][side 2][3][64] = 24 KB at the start of the x buffer (not
+// yet in use; the ghost sites it overlaps are cleared before x is stored).
+__device__ __forceinline__ int face_site(int mu, int side, int f) {
+  const int lo = f & ((1 << (2 * mu)) - 1);
+  const int hi = f >> (2 * mu);
+  return lo | ((side ? 0 : 3) << (2 * mu)) | (hi << (2 * mu + 2));
+}
+__device__ __forceinline__ int face_index(int mu, int s) {
+  const int lo = s & ((1 << (2 * mu)) - 1);
+  const int hi = s >> (2 * mu + 2);
+  return lo | (hi << (2 * mu));
+}
+__device__ __forceinline__ float4* face_slot(float4* slots, int mu, int side, int k, int f) {
+  return slots + ((mu * 2 + side) * 3 + k) * 64 + f;
+}
+
 template <int MU, bool HALF, typename SIO>
-__device__ __forceinline__ void st_inter(const Geom& g, const SIO& x, const unsigned char* links, int dom, int s,
-                                         int rhs_off, Spinor<float>& acc) {
+__device__ __forceinline__ void st_face_task(const Geom& g, const SIO& x, const unsigned char* links, int dom,
+                                             int rhs_off, int side, int f, float4* slots) {
   constexpr int step = 1 << (2 * MU);
-  const int c = lc<MU>(s);
   constexpr size_t dom_bytes = StageT<HALF>::LINK_BYTES;
-  if (c == 3) {
-    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU);
-    const int sign = ((__ldg(g.tflag + dom) >> (2 * MU)) & 1) ? g.bc_t : 1;
-    Spinor<float> p;
+  const int s = face_site(MU, side, f);
+  const int nd = __ldg(g.nbr + dom * 8 + 2 * MU + side);
+  const int sign = ((__ldg(g.tflag + dom) >> (2 * MU + side)) & 1) ? g.bc_t : 1;
+  Spinor<float> p;
+  HalfSpinor<float> h, uh;
+  if (side == 0) {
     x.load(g, nd + rhs_off, s - 3 * step, p);
-    HalfSpinor<float> h, uh;
     project<MU, -1>(p, h);
     const SU3<float> u = StageT<HALF>::link(links + dom * dom_bytes, MU, s);
     su3_mul(u, h, uh);
-    if (sign < 0) scale_half(uh, -1.0f);
-    accumulate<MU, -1>(acc, uh);
-  }
-  if (c == 0) {
-    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU + 1);
-    const int sign = ((__ldg(g.tflag + dom) >> (2 * MU + 1)) & 1) ? g.bc_t : 1;
+  } else {
     const int ns = s + 3 * step;
-    Spinor<float> p;
     x.load(g, nd + rhs_off, ns, p);
-    HalfSpinor<float> h, uh;
     project<MU, +1>(p, h);
     const SU3<float> u = StageT<HALF>::link(links + nd * dom_bytes, MU, ns);
     su3_dag_mul(u, h, uh);
-    if (sign < 0) scale_half(uh, -1.0f);
-    accumulate<MU, +1>(acc, uh);
   }
+  if (sign < 0) scale_half(uh, -1.0f);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const cx<float> a0 = uh.h[(2 * k) / 3][(2 * k) % 3];
+    const cx<float> a1 = uh.h[(2 * k + 1) / 3][(2 * k + 1) % 3];
+    *face_slot(slots, MU, side, k, f) = make_float4(a0.re, a0.im, a1.re, a1.im);
+  }
+}
+
+template <int MU>
+__device__ __forceinline__ void st_face_take(const float4* slots, int s, Spinor<float>& acc) {
+  const int c = lc<MU>(s);
+  if (c == 3 || c == 0) {
+    const int side = c == 0;
+    const int f = face_index(MU, s);
+    HalfSpinor<float> uh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 v = *face_slot(const_cast<float4*>(slots), MU, side, k, f);
+      uh.h[(2 * k) / 3][(2 * k) % 3] = make_cx(v.x, v.y);
+      uh.h[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v.z, v.w);
+    }
+    if (side == 0) accumulate<MU, -1>(acc, uh);
+    else accumulate<MU, +1>(acc, uh);
+  }
+}
+
+// all 512 face hops of the domain, then each site's sum of its face slots
+template <bool HALF, typename SIO>
+__device__ __forceinline__ void st_surface(const Geom& g, const SIO& x, const unsigned char* links, int dom,
+                                           int rhs_off, int s, float4* slots, Spinor<float>& acc) {
+  const int w = s >> 5;
+  const int side = (w >> 1) & 1;
+  const int f = ((w & 1) << 5) | (s & 31);
+  if (w < 4) {
+    st_face_task<0, HALF>(g, x, links, dom, rhs_off, side, f, slots);
+    st_face_task<2, HALF>(g, x, links, dom, rhs_off, side, f, slots);
+  } else {
+    st_face_task<1, HALF>(g, x, links, dom, rhs_off, side, f, slots);
+    st_face_task<3, HALF>(g, x, links, dom, rhs_off, side, f, slots);
+  }
+  __syncthreads();
+  st_face_take<0>(slots, s, acc);
+  st_face_take<1>(slots, s, acc);
+  st_face_take<2>(slots, s, acc);
+  st_face_take<3>(slots, s, acc);
 }
 
 template <bool HALF>
@@ -232,7 +323,7 @@ __device__ __forceinline__ void st_store_x(float4* sx, int s, const Spinor<float
   for (int k = 0; k < 6; ++k) {
     const cx<float> a0 = a.v[(2 * k) / 3][(2 * k) % 3];
     const cx<float> a1 = a.v[(2 * k + 1) / 3][(2 * k + 1) % 3];
-    sx[k * 256 + s] = make_float4(a0.re, a0.im, a1.re, a1.im);
+    sx[k * SX_STRIDE + s] = make_float4(a0.re, a0.im, a1.re, a1.im);
   }
 }
 
@@ -242,7 +333,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   extern __shared__ __align__(128) unsigned char smem[];
   using ST = StageT<HALF>;
   float4* sx = reinterpret_cast<float4*>(smem);                              // 24 KB
-  unsigned char* sl = smem + 6 * 256 * 16;                                    // links
+  unsigned char* sl = smem + SX_BYTES;                                        // links
   unsigned char* sc = sl + ST::LINK_BYTES;                                     // C_inv
   uint64_t* bar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);
   const Geom& g = a.g;
@@ -259,16 +350,12 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   for (int r = 0; r < a.nrhs; ++r) {
     const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
     const int rhs_off = r * g.ndom;
+    if (r > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
     Spinor<float> src;
     a.s_in.load(g, domr, s, src);
     Spinor<float> acc;
     zero(acc);
-    if (a.do_surface) {
-      st_inter<0, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
-      st_inter<1, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
-      st_inter<2, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
-      st_inter<3, HALF>(g, a.x, a.links, dom, s, rhs_off, acc);
-    }
+    if (a.do_surface) st_surface<HALF>(g, a.x, a.links, dom, rhs_off, s, sx, acc);
     if (r == 0) {
       __syncthreads();  // barrier initialisation visible to every thread
       const bool ok = mbar_wait_bounded(bar, 0);
@@ -279,8 +366,8 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
         if (!ok) mbar_wait_bounded(bar, 0);
         return;
       }
-    } else {
-      __syncthreads();  // every thread is done with the previous rhs's x in shared memory
+    } else if (a.do_surface) {
+      __syncthreads();  // every thread has taken its face slots before x overwrites them
     }
     if (a.do_surface) {
       st_clover<HALF>(sc, s, acc);
@@ -292,6 +379,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
           src.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
         }
     }
+    if (s < 6) sx[s * SX_STRIDE + SX_GHOST] = make_float4(0.f, 0.f, 0.f, 0.f);  // face slots overlap it
     st_store_x(sx, s, src);
     __syncthreads();
 
@@ -386,8 +474,8 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_link32, nd * StageT<false>::LINK_BYTES));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov16, nd * StageT<true>::CLOV_BYTES));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov32, nd * StageT<false>::CLOV_BYTES));
-    const int s16 = 6 * 256 * 16 + StageT<true>::LINK_BYTES + StageT<true>::CLOV_BYTES + 16;
-    const int s32 = 6 * 256 * 16 + StageT<false>::LINK_BYTES + StageT<false>::CLOV_BYTES + 16;
+    const int s16 = SX_BYTES + StageT<true>::LINK_BYTES + StageT<true>::CLOV_BYTES + 16;
+    const int s32 = SX_BYTES + StageT<false>::LINK_BYTES + StageT<false>::CLOV_BYTES + 16;
     QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F16Spinor>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
     QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F32Spinor>,
@@ -417,7 +505,7 @@ static void staged_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spino
   a.links = (const unsigned char*)(HALF ? ctx->st_link16 : ctx->st_link32);
   a.clov = (const unsigned char*)(HALF ? ctx->st_clov16 : ctx->st_clov32);
   a.status = ctx->d_status;
-  const int smem = 6 * 256 * 16 + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 16;
+  const int smem = SX_BYTES + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 16;
   for (int sweep = 0; sweep <= n_sap; ++sweep) {
     a.s_in = sweep == 0 ? s_first_in : s;
     a.do_update = sweep == n_sap ? 0 : 1;
