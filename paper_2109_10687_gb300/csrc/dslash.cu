@@ -81,6 +81,63 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const SIO& in, const LP& 
   }
 }
 
+// Both hops of direction MU without branches: the neighbour (domain, site)
+// and the boundary sign are selected, not branched on, so that the loads of
+// all eight hops are independent straight-line code the compiler can issue
+// early (the operator is bound by how many loads are in flight).  nb holds
+// the eight neighbour domains of dom, tf its boundary-sign flags.
+template <int MU, int PMF, int PMB, typename R, typename SIO, typename LP>
+__device__ __forceinline__ void hop_dir_bf(const Geom& g, const SIO& in, const LP& U, int dom, int s, int rhs_off,
+                                           const int nb[8], int tf, Spinor<R>& acc) {
+  const int c = (s >> g.shift[MU]) & (g.d[MU] - 1);
+  const int step = 1 << g.shift[MU];
+  const int span = (g.d[MU] - 1) * step;
+  {
+    const bool inside = c < g.d[MU] - 1;
+    const int nd = inside ? dom : nb[2 * MU];
+    const int ns = inside ? s + step : s - span;
+    const R f = (!inside && ((tf >> (2 * MU)) & 1)) ? R(g.bc_t) : R(1.0f);
+    Spinor<R> p;
+    in.load(g, nd + rhs_off, ns, p);
+    HalfSpinor<R> h, uh;
+    project<MU, PMF>(p, h);
+    SU3<R> u;
+    U.load(g, dom, MU, s, u);
+    su3_mul(u, h, uh);
+    accumulate<MU, PMF>(acc, uh, f);
+  }
+  {
+    const bool inside = c > 0;
+    const int nd = inside ? dom : nb[2 * MU + 1];
+    const int ns = inside ? s - step : s + span;
+    const R f = (!inside && ((tf >> (2 * MU + 1)) & 1)) ? R(g.bc_t) : R(1.0f);
+    Spinor<R> p;
+    in.load(g, nd + rhs_off, ns, p);
+    HalfSpinor<R> h, uh;
+    project<MU, PMB>(p, h);
+    SU3<R> u;
+    U.load(g, nd, MU, ns, u);
+    su3_dag_mul(u, h, uh);
+    accumulate<MU, PMB>(acc, uh, f);
+  }
+}
+
+template <int PMF, int PMB, typename R, typename SIO, typename LP>
+__device__ __forceinline__ void hopping_bf(const Geom& g, const SIO& in, const LP& U, int dom, int s, int rhs_off,
+                                           Spinor<R>& acc) {
+  int nb[8];
+  const int4 n0 = __ldg(reinterpret_cast<const int4*>(g.nbr) + 2 * dom);
+  const int4 n1 = __ldg(reinterpret_cast<const int4*>(g.nbr) + 2 * dom + 1);
+  nb[0] = n0.x; nb[1] = n0.y; nb[2] = n0.z; nb[3] = n0.w;
+  nb[4] = n1.x; nb[5] = n1.y; nb[6] = n1.z; nb[7] = n1.w;
+  const int tf = __ldg(g.tflag + dom);
+  zero(acc);
+  hop_dir_bf<0, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
+  hop_dir_bf<1, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
+  hop_dir_bf<2, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
+  hop_dir_bf<3, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
+}
+
 template <int PMF, int PMB, int FILTER, typename R, typename SIO, typename LP>
 __device__ __forceinline__ void hopping(const Geom& g, const SIO& in, const LP& U, int dom, int s, int rhs_off,
                                         Spinor<R>& acc) {
@@ -111,8 +168,8 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const typename Prec<R
   const int s = (int)(gid & (g.vd - 1));
   const int rhs_off = rhs * g.ndom;
   Spinor<R> acc;
-  if (MODE == MODE_DDAG) hopping<+1, -1, 0>(g, in, U, dom, s, rhs_off, acc);
-  else hopping<-1, +1, 0>(g, in, U, dom, s, rhs_off, acc);
+  if (MODE == MODE_DDAG) hopping_bf<+1, -1>(g, in, U, dom, s, rhs_off, acc);
+  else hopping_bf<-1, +1>(g, in, U, dom, s, rhs_off, acc);
   Spinor<R> x;
   in.load(g, dom + rhs_off, s, x);
   if constexpr (HINT) {
@@ -310,44 +367,61 @@ void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col
 // ---------------------------------------------------------------------------
 // D in double-float with the work of a site split over its three colour rows
 // ---------------------------------------------------------------------------
-// Thread (site, a) forms row a of every hop product U h and of the clover
-// multiply, so a thread holds one colour of the accumulator (4 spins) instead
-// of all twelve components; three times as many threads with a third of the
-// live state keep the long double-float dependency chains overlapped.
-// Block (32, 3, 2): warps of 32 consecutive sites share one colour row.
+// Thread (site, a) owns colour a of the site.  Phase 1: for each of the eight
+// hops it loads colour a of the neighbour spinor (four spins), projects it to
+// the two spin rows of that colour and leaves them in shared memory.
+// Phase 2: for each hop it reads the projected rows of all three colours,
+// forms row a of U h (or U^dag h) and rebuilds its four spins.  Each
+// projection is done once (not once per colour thread), and a thread loads
+// a third of every neighbour spinor.  Block (32, 3, 2): warps of 32
+// consecutive sites share one colour; 64 sites per block.
+constexpr int DF_SITES = 64;
+
+// neighbour (domain, site, sign) of hop (MU, FWD), selected without branches
 template <int MU, bool FWD>
-__device__ __forceinline__ void df_hop(const Geom& g, const DF64Spinor& in, const LinkPtr<df64>& U, int dom, int s,
-                                       int a, cx<df64> acc[4]) {
+__device__ __forceinline__ void df_nbr(const Geom& g, int dom, int s, const int nb[8], int tf, int& nd, int& ns,
+                                       bool& neg) {
+  const int c = (s >> g.shift[MU]) & (g.d[MU] - 1);
+  const int step = 1 << g.shift[MU];
+  const int span = (g.d[MU] - 1) * step;
+  const bool inside = FWD ? c < g.d[MU] - 1 : c > 0;
+  nd = inside ? dom : nb[2 * MU + (FWD ? 0 : 1)];
+  ns = inside ? (FWD ? s + step : s - step) : (FWD ? s - span : s + span);
+  neg = !inside && ((tf >> (2 * MU + (FWD ? 0 : 1))) & 1) && g.bc_t < 0;
+}
+
+__device__ __forceinline__ float4 df_pack(cx<df64> v) { return make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
+__device__ __forceinline__ cx<df64> df_unpack(float4 v) { return make_cx(df64(v.x, v.y), df64(v.z, v.w)); }
+
+// phase 1: rows (h0, h1) of colour a of the projected neighbour, signed
+template <int MU, bool FWD>
+__device__ __forceinline__ void df_project(const Geom& g, const DF64Spinor& in, int dom, int s, int a,
+                                           const int nb[8], int tf, float4* sh, int sl) {
   int nd, ns;
-  const int sign = nbr_site(g, dom, s, MU, FWD, nd, ns);
-  constexpr int PM = FWD ? -1 : +1;
-  // projected neighbour, all colours: h[spin row][colour]
-  HalfSpinor<df64> h;
+  bool neg;
+  df_nbr<MU, FWD>(g, dom, s, nb, tf, nd, ns, neg);
+  cx<df64> q[4];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Spinor<df64> p;  // only colour c of the spinor is filled
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp) {
-      const float4 v = __ldg(in.p + in.idx(g, nd, sp * 3 + c, ns));
-      p.v[sp][c] = make_cx(df64(v.x, v.y), df64(v.z, v.w));
-    }
-    // project colour c only (the projector acts on spin, colour by colour)
-    const cx<df64> u0 = p.v[0][c], u1 = p.v[1][c], l0 = p.v[2][c], l1 = p.v[3][c];
-    if (MU == 0) {
-      if (PM < 0) { h.h[0][c] = u0 + times_i(l1); h.h[1][c] = u1 + times_i(l0); }
-      else        { h.h[0][c] = u0 - times_i(l1); h.h[1][c] = u1 - times_i(l0); }
-    } else if (MU == 1) {
-      if (PM < 0) { h.h[0][c] = u0 + l1; h.h[1][c] = u1 - l0; }
-      else        { h.h[0][c] = u0 - l1; h.h[1][c] = u1 + l0; }
-    } else if (MU == 2) {
-      if (PM < 0) { h.h[0][c] = u0 + times_i(l0); h.h[1][c] = u1 - times_i(l1); }
-      else        { h.h[0][c] = u0 - times_i(l0); h.h[1][c] = u1 + times_i(l1); }
-    } else {
-      if (PM < 0) { h.h[0][c] = u0 - l0; h.h[1][c] = u1 - l1; }
-      else        { h.h[0][c] = u0 + l0; h.h[1][c] = u1 + l1; }
-    }
+  for (int sp = 0; sp < 4; ++sp) q[sp] = df_unpack(__ldg(in.p + in.idx(g, nd, sp * 3 + a, ns)));
+  cx<df64> h0, h1;
+  project1<MU, FWD ? -1 : +1>(q[0], q[1], q[2], q[3], h0, h1);
+  if (neg) {  // exact: a sign flip of both parts
+    h0 = make_cx(-h0.re, -h0.im);
+    h1 = make_cx(-h1.re, -h1.im);
   }
-  // row a of U (forward) or of U^dag (backward: column a of U(n - mu), conjugated)
+  constexpr int hop = 2 * MU + (FWD ? 0 : 1);
+  sh[((hop * 2 + 0) * 3 + a) * DF_SITES + sl] = df_pack(h0);
+  sh[((hop * 2 + 1) * 3 + a) * DF_SITES + sl] = df_pack(h1);
+}
+
+// phase 2: row a of U h (forward) or U^dag h (backward), rebuilt into colour a
+template <int MU, bool FWD>
+__device__ __forceinline__ void df_mul_acc(const Geom& g, const LinkPtr<df64>& U, int dom, int s, int a,
+                                           const int nb[8], int tf, const float4* sh, int sl, cx<df64> acc[4]) {
+  int nd, ns;
+  bool neg;
+  df_nbr<MU, FWD>(g, dom, s, nb, tf, nd, ns, neg);
+  constexpr int hop = 2 * MU + (FWD ? 0 : 1);
   cx<df64> row[3];
   {
     const size_t base = ((size_t)(((FWD ? dom : nd) * 4 + MU) * 9)) << g.logvd;
@@ -362,12 +436,13 @@ __device__ __forceinline__ void df_hop(const Geom& g, const DF64Spinor& in, cons
   cx<df64> uh[2];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    cx<df64> t = row[0] * h.h[r][0];
-    t = cmac(t, row[1], h.h[r][1]);
-    t = cmac(t, row[2], h.h[r][2]);
-    uh[r] = sign < 0 ? -t : t;
+    cx<df64> t = row[0] * df_unpack(sh[((hop * 2 + r) * 3 + 0) * DF_SITES + sl]);
+    t = cmac(t, row[1], df_unpack(sh[((hop * 2 + r) * 3 + 1) * DF_SITES + sl]));
+    t = cmac(t, row[2], df_unpack(sh[((hop * 2 + r) * 3 + 2) * DF_SITES + sl]));
+    uh[r] = t;
   }
-  // rebuild the four spins of colour a (same rules as accumulate())
+  // rebuild the four spins of colour a (the rules of accumulate())
+  constexpr int PM = FWD ? -1 : +1;
   const cx<df64> h0 = uh[0], h1 = uh[1];
   acc[0] = acc[0] + h0;
   acc[1] = acc[1] + h1;
@@ -393,10 +468,7 @@ __device__ __forceinline__ void df_clover_rows(const Geom& g, const DF64Spinor& 
   for (int b = 0; b < 2; ++b) {
     cx<df64> xv[6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const float4 v = __ldg(in.p + in.idx(g, dom, (2 * b + j / 3) * 3 + j % 3, s));
-      xv[j] = make_cx(df64(v.x, v.y), df64(v.z, v.w));
-    }
+    for (int j = 0; j < 6; ++j) xv[j] = df_unpack(__ldg(in.p + in.idx(g, dom, (2 * b + j / 3) * 3 + j % 3, s)));
     CloverBlockDF64 blk;
     clov.load_block(g, dom, s, b, blk);
 #pragma unroll
@@ -417,25 +489,48 @@ __device__ __forceinline__ void df_clover_rows(const Geom& g, const DF64Spinor& 
 __global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
                                                                 LinkPtr<df64> U, CloverPtrDF64 clov, df64 kappa,
                                                                 int nrhs) {
+  __shared__ float4 sh[8 * 2 * 3 * DF_SITES];  // projected rows [hop][row][colour][site], 48 KB
   const int a = threadIdx.y;  // colour row
+  const int sl = threadIdx.z * 32 + threadIdx.x;
   const int rhs = blockIdx.x % nrhs;
-  const long long gid = (blockIdx.x / nrhs) * 64LL + threadIdx.z * 32 + threadIdx.x;
-  if (gid >= g.vol) return;
-  const int dom = __ldg(g.lex2dom + (int)(gid >> g.logvd));
-  const int s = (int)(gid & (g.vd - 1));
+  const long long gid = (blockIdx.x / nrhs) * (long long)DF_SITES + sl;
+  // every thread takes part in the barrier; sites past the end compute on
+  // site 0 of the block's range and store nothing
+  const bool live = gid < g.vol;
+  const long long gq = live ? gid : (blockIdx.x / nrhs) * (long long)DF_SITES;
+  const int dom = __ldg(g.lex2dom + (int)(gq >> g.logvd));
+  const int s = (int)(gq & (g.vd - 1));
   const int rhs_off = rhs * g.ndom;
   const DF64Spinor inr{in.p + ((size_t)rhs_off * 12 << g.logvd)};
+  int nb[8];
+  {
+    const int4 n0 = __ldg(reinterpret_cast<const int4*>(g.nbr) + 2 * dom);
+    const int4 n1 = __ldg(reinterpret_cast<const int4*>(g.nbr) + 2 * dom + 1);
+    nb[0] = n0.x; nb[1] = n0.y; nb[2] = n0.z; nb[3] = n0.w;
+    nb[4] = n1.x; nb[5] = n1.y; nb[6] = n1.z; nb[7] = n1.w;
+  }
+  const int tf = __ldg(g.tflag + dom);
+  df_project<0, true>(g, inr, dom, s, a, nb, tf, sh, sl);
+  df_project<0, false>(g, inr, dom, s, a, nb, tf, sh, sl);
+  df_project<1, true>(g, inr, dom, s, a, nb, tf, sh, sl);
+  df_project<1, false>(g, inr, dom, s, a, nb, tf, sh, sl);
+  df_project<2, true>(g, inr, dom, s, a, nb, tf, sh, sl);
+  df_project<2, false>(g, inr, dom, s, a, nb, tf, sh, sl);
+  df_project<3, true>(g, inr, dom, s, a, nb, tf, sh, sl);
+  df_project<3, false>(g, inr, dom, s, a, nb, tf, sh, sl);
+  __syncthreads();
   cx<df64> acc[4];
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) acc[sp] = make_cx(df64(0.f), df64(0.f));
-  df_hop<0, true>(g, inr, U, dom, s, a, acc);
-  df_hop<0, false>(g, inr, U, dom, s, a, acc);
-  df_hop<1, true>(g, inr, U, dom, s, a, acc);
-  df_hop<1, false>(g, inr, U, dom, s, a, acc);
-  df_hop<2, true>(g, inr, U, dom, s, a, acc);
-  df_hop<2, false>(g, inr, U, dom, s, a, acc);
-  df_hop<3, true>(g, inr, U, dom, s, a, acc);
-  df_hop<3, false>(g, inr, U, dom, s, a, acc);
+  df_mul_acc<0, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  df_mul_acc<0, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  df_mul_acc<1, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  df_mul_acc<1, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  df_mul_acc<2, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  df_mul_acc<2, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  df_mul_acc<3, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  df_mul_acc<3, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+  if (!live) return;
   // (1 + C) x, rows (block b, spin-in-block r, colour a): index i = 3 r + a;
   // a is warp-uniform, and a compile-time row keeps the block in registers
   cx<df64> res[4];
@@ -447,7 +542,7 @@ __global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spin
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) {
     const cx<df64> o = make_cx(fma(-kappa, acc[sp].re, res[sp].re), fma(-kappa, acc[sp].im, res[sp].im));
-    out.p[out.idx(g, dom + rhs_off, sp * 3 + a, s)] = make_float4(o.re.hi, o.re.lo, o.im.hi, o.im.lo);
+    out.p[out.idx(g, dom + rhs_off, sp * 3 + a, s)] = df_pack(o);
   }
 }
 

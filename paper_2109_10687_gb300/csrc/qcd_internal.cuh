@@ -204,48 +204,63 @@ __device__ __forceinline__ void zero(Spinor<R>& a) {
 // returns the two independent spin rows h (the upper half of the projected
 // spinor); accumulate() adds the full projected spinor rebuilt from U h.
 // ---------------------------------------------------------------------------
+// one colour: (u0, u1, l0, l1) are the four spins of that colour
 template <int MU, int PM, typename R>
-__device__ __forceinline__ void project(const Spinor<R>& p, HalfSpinor<R>& h) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const cx<R> u0 = p.v[0][c], u1 = p.v[1][c], l0 = p.v[2][c], l1 = p.v[3][c];
-    if (MU == 0) {
-      if (PM < 0) { h.h[0][c] = u0 + times_i(l1); h.h[1][c] = u1 + times_i(l0); }
-      else        { h.h[0][c] = u0 - times_i(l1); h.h[1][c] = u1 - times_i(l0); }
-    } else if (MU == 1) {
-      if (PM < 0) { h.h[0][c] = u0 + l1; h.h[1][c] = u1 - l0; }
-      else        { h.h[0][c] = u0 - l1; h.h[1][c] = u1 + l0; }
-    } else if (MU == 2) {
-      if (PM < 0) { h.h[0][c] = u0 + times_i(l0); h.h[1][c] = u1 - times_i(l1); }
-      else        { h.h[0][c] = u0 - times_i(l0); h.h[1][c] = u1 + times_i(l1); }
-    } else {
-      if (PM < 0) { h.h[0][c] = u0 - l0; h.h[1][c] = u1 - l1; }
-      else        { h.h[0][c] = u0 + l0; h.h[1][c] = u1 + l1; }
-    }
+__device__ __forceinline__ void project1(cx<R> u0, cx<R> u1, cx<R> l0, cx<R> l1, cx<R>& h0, cx<R>& h1) {
+  if (MU == 0) {
+    if (PM < 0) { h0 = u0 + times_i(l1); h1 = u1 + times_i(l0); }
+    else        { h0 = u0 - times_i(l1); h1 = u1 - times_i(l0); }
+  } else if (MU == 1) {
+    if (PM < 0) { h0 = u0 + l1; h1 = u1 - l0; }
+    else        { h0 = u0 - l1; h1 = u1 + l0; }
+  } else if (MU == 2) {
+    if (PM < 0) { h0 = u0 + times_i(l0); h1 = u1 - times_i(l1); }
+    else        { h0 = u0 - times_i(l0); h1 = u1 + times_i(l1); }
+  } else {
+    if (PM < 0) { h0 = u0 - l0; h1 = u1 - l1; }
+    else        { h0 = u0 + l0; h1 = u1 + l1; }
   }
 }
 
 template <int MU, int PM, typename R>
-__device__ __forceinline__ void accumulate(Spinor<R>& acc, const HalfSpinor<R>& h) {
+__device__ __forceinline__ void project(const Spinor<R>& p, HalfSpinor<R>& h) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const cx<R> h0 = h.h[0][c], h1 = h.h[1][c];
-    acc.v[0][c] = acc.v[0][c] + h0;
-    acc.v[1][c] = acc.v[1][c] + h1;
-    if (MU == 0) {
-      if (PM < 0) { acc.v[2][c] = acc.v[2][c] + times_mi(h1); acc.v[3][c] = acc.v[3][c] + times_mi(h0); }
-      else        { acc.v[2][c] = acc.v[2][c] + times_i(h1);  acc.v[3][c] = acc.v[3][c] + times_i(h0); }
-    } else if (MU == 1) {
-      if (PM < 0) { acc.v[2][c] = acc.v[2][c] - h1; acc.v[3][c] = acc.v[3][c] + h0; }
-      else        { acc.v[2][c] = acc.v[2][c] + h1; acc.v[3][c] = acc.v[3][c] - h0; }
-    } else if (MU == 2) {
-      if (PM < 0) { acc.v[2][c] = acc.v[2][c] + times_mi(h0); acc.v[3][c] = acc.v[3][c] + times_i(h1); }
-      else        { acc.v[2][c] = acc.v[2][c] + times_i(h0);  acc.v[3][c] = acc.v[3][c] + times_mi(h1); }
-    } else {
-      if (PM < 0) { acc.v[2][c] = acc.v[2][c] - h0; acc.v[3][c] = acc.v[3][c] - h1; }
-      else        { acc.v[2][c] = acc.v[2][c] + h0; acc.v[3][c] = acc.v[3][c] + h1; }
-    }
+  for (int c = 0; c < 3; ++c) project1<MU, PM>(p.v[0][c], p.v[1][c], p.v[2][c], p.v[3][c], h.h[0][c], h.h[1][c]);
+}
+
+// a + f x for a real factor f
+template <typename R>
+__device__ __forceinline__ cx<R> cfma(R f, const cx<R>& x, const cx<R>& a) {
+  return make_cx<R>(fma(f, x.re, a.re), fma(f, x.im, a.im));
+}
+
+// one colour: a[sp] += f * (spin sp of the spinor rebuilt from (h0, h1))
+template <int MU, int PM, typename R>
+__device__ __forceinline__ void accumulate1(cx<R>& a0, cx<R>& a1, cx<R>& a2, cx<R>& a3, cx<R> h0, cx<R> h1, R f) {
+  a0 = cfma(f, h0, a0);
+  a1 = cfma(f, h1, a1);
+  if (MU == 0) {
+    if (PM < 0) { a2 = cfma(f, times_mi(h1), a2); a3 = cfma(f, times_mi(h0), a3); }
+    else        { a2 = cfma(f, times_i(h1), a2);  a3 = cfma(f, times_i(h0), a3); }
+  } else if (MU == 1) {
+    if (PM < 0) { a2 = cfma(-f, h1, a2); a3 = cfma(f, h0, a3); }
+    else        { a2 = cfma(f, h1, a2);  a3 = cfma(-f, h0, a3); }
+  } else if (MU == 2) {
+    if (PM < 0) { a2 = cfma(f, times_mi(h0), a2); a3 = cfma(f, times_i(h1), a3); }
+    else        { a2 = cfma(f, times_i(h0), a2);  a3 = cfma(f, times_mi(h1), a3); }
+  } else {
+    if (PM < 0) { a2 = cfma(-f, h0, a2); a3 = cfma(-f, h1, a3); }
+    else        { a2 = cfma(f, h0, a2);  a3 = cfma(f, h1, a3); }
   }
+}
+
+// acc += f * (projected spinor rebuilt from h); f = 1 unless a hop carries
+// the antiperiodic sign (a constant 1 folds to plain additions)
+template <int MU, int PM, typename R>
+__device__ __forceinline__ void accumulate(Spinor<R>& acc, const HalfSpinor<R>& h, R f = R(1.0f)) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    accumulate1<MU, PM>(acc.v[0][c], acc.v[1][c], acc.v[2][c], acc.v[3][c], h.h[0][c], h.h[1][c], f);
 }
 
 // y = U h (both spin rows) or y = U^dag h

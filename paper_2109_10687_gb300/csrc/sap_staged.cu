@@ -387,10 +387,12 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
     const int napp = a.n_jac + (a.do_update ? 1 : 0);
     for (int it = 0; it < napp; ++it) {
       zero(acc);
+      // t first: its warp-uniform branches then precede one straight-line
+      // stretch (x, y, z hops and the clover multiply) the compiler can schedule
+      st_intra<3, HALF>(sx, sl, s, acc);
       st_intra<0, HALF>(sx, sl, s, acc);
       st_intra<1, HALF>(sx, sl, s, acc);
       st_intra<2, HALF>(sx, sl, s, acc);
-      st_intra<3, HALF>(sx, sl, s, acc);
       st_clover<HALF>(sc, s, acc);
       if (it < a.n_jac) {
 #pragma unroll
