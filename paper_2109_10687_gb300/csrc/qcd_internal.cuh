@@ -703,8 +703,8 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st);
 bool sap_staged_available(const qcd_ctx* ctx);
 void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
                              int n_sap, int n_jac, cudaStream_t st);
-void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int nrhs,
-                             int n_sap, int n_jac, cudaStream_t st);
+void sap_staged_sequence_f16(qcd_ctx* ctx, F32Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b,
+                             F32Spinor x_out, int nrhs, int n_sap, int n_jac, cudaStream_t st);
 void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
                               int n_sap, int n_jac, cudaStream_t st);
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,

@@ -305,22 +305,25 @@ void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_
   F16Spinor x16{(uint4*)ws_x16, (float*)((uint4*)ws_x16 + 3 * nv)};
   F16Spinor b16{(uint4*)ws_b16, (float*)((uint4*)ws_b16 + 3 * nv)};
   const dim3 cgrid(grid_for(g.vol, 256), nrhs);
+  if (staged) {
+    // the first sweep reads the float32 source and the last one writes the
+    // float32 result: no conversion launches
+    sap_staged_sequence_f16(ctx, F32Spinor{(float4*)b}, s16, x16, F32Spinor{(float4*)b}, F32Spinor{x}, nrhs, n_sap,
+                            n_jac, st);
+    return;
+  }
   {
     LaunchScope ls(ctx, QCD_KC_BLAS, st);
     f32_to_f16_kernel<<<cgrid, 256, 0, st>>>(g, b16, F32Spinor{(float4*)b});
     check_launch();
   }
-  if (staged) {
-    sap_staged_sequence_f16(ctx, b16, s16, x16, F32Spinor{(float4*)b}, nrhs, n_sap, n_jac, st);
-  } else {
-    for (int r = 0; r < nrhs; ++r) {
-      F16Spinor sr{s16.p + 3 * v * r, s16.nrm + v * r};
-      F16Spinor xr{x16.p + 3 * v * r, x16.nrm + v * r};
-      F16Spinor br{b16.p + 3 * v * r, b16.nrm + v * r};
-      sap_sequence<F16Spinor, LinkPtrHalf, CloverPtrF16, CloverBlockF32>(
-          ctx, br, sr, xr, F32Spinor{(float4*)b + r * v4}, LinkPtrHalf{ctx->u16}, CloverPtrF16{ctx->cinv16}, n_sap,
-          n_jac, st);
-    }
+  for (int r = 0; r < nrhs; ++r) {
+    F16Spinor sr{s16.p + 3 * v * r, s16.nrm + v * r};
+    F16Spinor xr{x16.p + 3 * v * r, x16.nrm + v * r};
+    F16Spinor br{b16.p + 3 * v * r, b16.nrm + v * r};
+    sap_sequence<F16Spinor, LinkPtrHalf, CloverPtrF16, CloverBlockF32>(
+        ctx, br, sr, xr, F32Spinor{(float4*)b + r * v4}, LinkPtrHalf{ctx->u16}, CloverPtrF16{ctx->cinv16}, n_sap,
+        n_jac, st);
   }
   {
     LaunchScope ls(ctx, QCD_KC_BLAS, st);

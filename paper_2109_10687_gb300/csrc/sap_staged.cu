@@ -92,6 +92,9 @@ struct StagedArgs {
   float kappa;
   SIO s_in, s_out, x;   // vectors: float16 or float32 storage, independent of HALF
   F32Spinor b;
+  F32Spinor s_in32;      // if set: the sweep's input is read from this float32 field instead of s_in
+  F32Spinor x_out32;     // if set: the iterate is also stored to this float32 field
+  int x_store;           // store the iterate in x (0 when no later launch reads it)
   const unsigned char* links;  // staging layout, all domains
   const unsigned char* clov;
   int* status;                 // word 0: set to QCD_ERR_TIMEOUT if a wait gives up
@@ -145,8 +148,8 @@ __device__ __forceinline__ int lc(int s) { return (s >> (2 * MU)) & 3; }
 // shared-memory x: float4 group k holds complex components 2k and 2k+1,
 // component c = spin * 3 + colour; row k has 256 sites and one zero "ghost"
 // site that hops leaving the domain read instead of a neighbour
-constexpr int SX_STRIDE = 257;
-constexpr int SX_GHOST = 256;
+constexpr int SX_STRIDE = 264;
+constexpr int SX_GHOST = 256;  // 8 zero sites, one per 16-byte bank group
 constexpr int SX_BYTES = 6 * SX_STRIDE * 16;
 __device__ __forceinline__ void st_load_x(const float4* sx, int site, Spinor<float>& p) {
 #pragma unroll
@@ -170,7 +173,7 @@ __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* 
   if (MU < 3) {
     {
       Spinor<float> p;
-      st_load_x(sx, c < 3 ? s + step : SX_GHOST, p);
+      st_load_x(sx, c < 3 ? s + step : SX_GHOST + ((s + step) & 7), p);
       HalfSpinor<float> h, uh;
       project<MU, -1>(p, h);
       const SU3<float> u = StageT<HALF>::link(sl, MU, s);
@@ -178,7 +181,7 @@ __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* 
       accumulate<MU, -1>(acc, uh);
     }
     {
-      const int nb = c > 0 ? s - step : SX_GHOST;
+      const int nb = c > 0 ? s - step : SX_GHOST + ((s - step) & 7);
       Spinor<float> p;
       st_load_x(sx, nb, p);
       HalfSpinor<float> h, uh;
@@ -352,7 +355,8 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
     const int rhs_off = r * g.ndom;
     if (r > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
     Spinor<float> src;
-    a.s_in.load(g, domr, s, src);
+    if (a.s_in32.p) a.s_in32.load(g, domr, s, src);
+    else a.s_in.load(g, domr, s, src);
     Spinor<float> acc;
     zero(acc);
     if (a.do_surface) st_surface<HALF>(g, a.x, a.links, dom, rhs_off, s, sx, acc);
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
           src.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
         }
     }
-    if (s < 6) sx[s * SX_STRIDE + SX_GHOST] = make_float4(0.f, 0.f, 0.f, 0.f);  // face slots overlap it
+    if (s < 48) sx[(s >> 3) * SX_STRIDE + SX_GHOST + (s & 7)] = make_float4(0.f, 0.f, 0.f, 0.f);  // face slots overlap it
     st_store_x(sx, s, src);
     __syncthreads();
 
@@ -420,7 +424,8 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
         a.s_out.store(g, domr, s, acc);
       }
     }
-    a.x.store(g, domr, s, xk);
+    if (a.x_store) a.x.store(g, domr, s, xk);
+    if (a.x_out32.p) a.x_out32.store(g, domr, s, xk);
   }
 }
 
@@ -493,9 +498,13 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
   check_launch();
 }
 
+// Algorithm 1 as 2 (n_sap + 1) launches.  s_first_in32 (float32) is the
+// first sweep's input, the source itself; x_out32, if set, receives the final
+// iterate in float32 (the last sweep of colour 0 also keeps x for the surface
+// term of the colour-1 launch that follows).
 template <bool HALF, typename SIO>
-static void staged_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spinor b, int nrhs, int n_sap, int n_jac,
-                            cudaStream_t st) {
+static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b, F32Spinor x_out32,
+                            int nrhs, int n_sap, int n_jac, cudaStream_t st) {
   StagedArgs<HALF, SIO> a;
   a.g = ctx->geom;
   a.nrhs = nrhs;
@@ -504,16 +513,20 @@ static void staged_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spino
   a.b = b;
   a.x = x;
   a.s_out = s;
+  a.s_in = s;
   a.links = (const unsigned char*)(HALF ? ctx->st_link16 : ctx->st_link32);
   a.clov = (const unsigned char*)(HALF ? ctx->st_clov16 : ctx->st_clov32);
   a.status = ctx->d_status;
   const int smem = SX_BYTES + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 16;
   for (int sweep = 0; sweep <= n_sap; ++sweep) {
-    a.s_in = sweep == 0 ? s_first_in : s;
+    a.s_in32 = sweep == 0 ? s_first_in32 : F32Spinor{nullptr};
     a.do_update = sweep == n_sap ? 0 : 1;
     for (int colour = 0; colour < 2; ++colour) {
       a.colour = colour;
       a.do_surface = (sweep == 0 && colour == 0) ? 0 : 1;
+      const bool last = sweep == n_sap;
+      a.x_out32 = last ? x_out32 : F32Spinor{nullptr};
+      a.x_store = (!last || !x_out32.p || colour == 0) ? 1 : 0;
       LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
       sap_staged_kernel<HALF, SIO><<<ctx->geom.nhalf, ST_THREADS, smem, st>>>(a);
       check_launch();
@@ -523,15 +536,15 @@ static void staged_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spino
 
 void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
                              int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<false, F32Spinor>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
+  staged_sequence<false, F32Spinor>(ctx, s_first_in, s, x, b, F32Spinor{nullptr}, nrhs, n_sap, n_jac, st);
 }
-void sap_staged_sequence_f16(qcd_ctx* ctx, F16Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b, int nrhs,
-                             int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<true, F16Spinor>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
+void sap_staged_sequence_f16(qcd_ctx* ctx, F32Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b,
+                             F32Spinor x_out, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+  staged_sequence<true, F16Spinor>(ctx, s_first_in, s, x, b, x_out, nrhs, n_sap, n_jac, st);
 }
 void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
                               int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<true, F32Spinor>(ctx, s_first_in, s, x, b, nrhs, n_sap, n_jac, st);
+  staged_sequence<true, F32Spinor>(ctx, s_first_in, s, x, b, F32Spinor{nullptr}, nrhs, n_sap, n_jac, st);
 }
 
 }  // namespace qcd
