@@ -290,9 +290,9 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2109_10687_gb300 import replicas
+
+    world, rank, local = replicas.rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -304,8 +304,9 @@ def main():
 
     _build.build()
     dev = torch.device("cuda", local)
-    u = random_su3_field(DIMS, EPS, GAUGE_SEED + rank)
-    b_np = gaussian_spinor(DIMS, SOURCE_SEED + rank)
+    gauge_seed, source_seed = replicas.replica_seeds(GAUGE_SEED, SOURCE_SEED, rank)
+    u = random_su3_field(DIMS, EPS, gauge_seed)
+    b_np = gaussian_spinor(DIMS, source_seed)
     lat = Lattice(DIMS, DOMAIN, -1, "chiral", dev).setup(u, KAPPA, CSW)
     del u
     b_dev = torch.view_as_real(torch.from_numpy(b_np)).to(dev).contiguous()
@@ -326,8 +327,7 @@ def main():
     P_F32 = params("single")
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier(world)
         torch.cuda.synchronize()
 
     def solve(p, xb=x_dev, bb=b_dev):
@@ -356,11 +356,8 @@ def main():
     barrier()
     launches = B.qcd_launch_count(lat.ctx) - launches0
     elapsed = ev0.elapsed_time(ev1) / 1000.0
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * args.steps / elapsed
+    elapsed = replicas.max_over_ranks(elapsed, world, device=dev)
+    value = replicas.job_throughput(world, args.steps, elapsed)
     ms_per_step = 1000.0 * elapsed / args.steps
     graph_ms = ms_per_step
 
@@ -433,9 +430,12 @@ def main():
         rc, _ = B.qcd_solve(lat.ctx, x_host, b_host, 1, P_MIX)
     barrier()
     e2e_s = (time.perf_counter() - te) / ne
-    e2e_value = world / e2e_s
+    e2e_s = replicas.max_over_ranks(e2e_s, world, device=dev)
+    e2e_value = replicas.job_throughput(world, 1, e2e_s)
 
     tuning = B.qcd_tuning_report(lat.ctx).strip().splitlines()
+    # float32 FMA throughput measured on this device (outside every timed region)
+    fma_tflops = B.qcd_measure_fp32_peak(lat.ctx)
 
     # dominant kernel by device time in the timed region
     sap_n, sap_ms = prof[B.KC_SAP_BLOCK]
@@ -475,6 +475,8 @@ def main():
                      "traffic": traffic, "flop_per_site": sap_flop_per_site(), "sites_per_launch": vol // 2,
                      "avg_launch_ms": sap_avg_ms, "share_of_device_time": sap_ms / total_ms if total_ms else None,
                      "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "measured_fp32_fma_tflops": fma_tflops,
+                     "frac_of_measured_fma": sap_tflops / fma_tflops if fma_tflops else None,
                      "hbm_view": {"bytes_per_site": sap_bytes_per_site("half"), "achieved_gbs": sap_gbs,
                                   "frac_of_measured": sap_gbs / peak}},
         "kernel_classes_ms": {name: prof[k][1] for k, name in

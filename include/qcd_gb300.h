@@ -312,6 +312,15 @@ int qcd_tuning_report(qcd_ctx* ctx, char* buf, size_t len);
 /* Number of kernels the library has launched on this context so far. */
 int qcd_launch_count(const qcd_ctx* ctx, long long* count);
 
+/* Measurement utility (no counterpart in the paper): the device's float32
+ * FMA throughput in TFLOP/s (2 flop per FMA), from a kernel of independent
+ * fused multiply-add chains over every SM, timed with CUDA events on
+ * `stream` (the best of three launches after a warm-up).  It is the
+ * denominator of the ALU roofline of the SAP block kernel.  Synchronises the
+ * stream; writes *tflops.  QCD_ERR_ARG for null pointers, QCD_ERR_CUDA on a
+ * CUDA error. */
+int qcd_measure_fp32_peak(qcd_ctx* ctx, double* tflops, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,7 @@ _SIGS = {
     "qcd_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.POINTER(SolveParams),
                              ctypes.POINTER(SolveInfo), _P]),
     "qcd_tuning_report": (_I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    "qcd_measure_fp32_peak": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 
@@ -281,6 +282,13 @@ def qcd_launch_count(ctx):
 
 def qcd_set_tuning(ctx, enable=True):
     return check(ctx, lib().qcd_set_tuning(ctx, int(bool(enable))))
+
+
+def qcd_measure_fp32_peak(ctx, stream=None):
+    """float32 FMA throughput of the device in TFLOP/s (measured)."""
+    v = ctypes.c_double()
+    check(ctx, lib().qcd_measure_fp32_peak(ctx, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def qcd_tuning_report(ctx):

@@ -4,6 +4,7 @@
 // keeps the fastest.  The shapes differ only in scheduling, never in the
 // arithmetic each site performs.
 
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <string>
@@ -86,5 +87,73 @@ extern "C" int qcd_tuning_report(qcd_ctx* ctx, char* buf, size_t len) {
     out += line;
   }
   std::snprintf(buf, len, "%s", out.c_str());
+  return QCD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// float32 FMA throughput (measurement utility)
+// ---------------------------------------------------------------------------
+namespace qcd {
+constexpr int FMA_CHAINS = 8;
+constexpr int FMA_UNROLL = 32;
+
+// each thread runs FMA_CHAINS independent chains x <- x a + b; with a < 1
+// and b > 0 the values stay in a normal range.  The result is stored only
+// if it equals a value it cannot reach, which keeps the work live.
+__global__ void __launch_bounds__(256) fma_peak_kernel(float* out, int iters, float a, float b) {
+  float x[FMA_CHAINS];
+#pragma unroll
+  for (int c = 0; c < FMA_CHAINS; ++c) x[c] = threadIdx.x * 1e-3f + c;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < FMA_UNROLL; ++u)
+#pragma unroll
+      for (int c = 0; c < FMA_CHAINS; ++c) x[c] = fmaf(x[c], a, b);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int c = 0; c < FMA_CHAINS; ++c) sum += x[c];
+  if (sum == -1.0f) out[blockIdx.x] = sum;
+}
+}  // namespace qcd
+
+extern "C" int qcd_measure_fp32_peak(qcd_ctx* ctx, double* tflops, void* stream) {
+  if (!ctx || !tflops) return QCD_ERR_ARG;
+  try {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0, nsm = 0;
+    QCD_CUDA_CHECK(cudaGetDevice(&dev));
+    QCD_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = nsm * 8, threads = 256, iters = 2048;
+    float* out = nullptr;
+    QCD_CUDA_CHECK(cudaMalloc(&out, sizeof(float) * blocks));
+    cudaEvent_t e0, e1;
+    QCD_CUDA_CHECK(cudaEventCreate(&e0));
+    QCD_CUDA_CHECK(cudaEventCreate(&e1));
+    fma_peak_kernel<<<blocks, threads, 0, st>>>(out, iters, 0.999f, 1e-3f);
+    double best = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      QCD_CUDA_CHECK(cudaEventRecord(e0, st));
+      fma_peak_kernel<<<blocks, threads, 0, st>>>(out, iters, 0.999f, 1e-3f);
+      QCD_CUDA_CHECK(cudaEventRecord(e1, st));
+      QCD_CUDA_CHECK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      QCD_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+      const double flop = 2.0 * blocks * threads * (double)iters * FMA_UNROLL * FMA_CHAINS;
+      if (ms > 0.f) best = std::max(best, flop / (ms * 1e-3) / 1e12);
+    }
+    ctx->launches += 4;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    check_launch();
+    *tflops = best;
+  } catch (const Error& e) {
+    ctx->err = e.msg;
+    return e.code;
+  } catch (...) {
+    ctx->err = "unknown error";
+    return QCD_ERR_CUDA;
+  }
   return QCD_OK;
 }

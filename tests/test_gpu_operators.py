@@ -131,3 +131,15 @@ def test_bad_geometry_rejected():
         B.qcd_create((8, 8, 8, 12), (4, 4, 4, 4))      # 12 is not a multiple of 2*4
     with pytest.raises(B.QcdError):
         B.qcd_create((12, 12, 12, 12), (3, 3, 3, 3))   # not a power of two
+
+
+def test_measure_fp32_peak_plausible():
+    """The FMA-loop measurement of the float32 peak lands near the derived
+    152 SMs x 128 lanes x 2 flop x clock (about 80 TFLOP/s at 2.07 GHz)."""
+    from paper_2109_10687_gb300 import binding as B
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), seed=1005, oracle=False)
+    try:
+        t = B.qcd_measure_fp32_peak(p.lat.ctx)
+        assert 20.0 < t < 120.0
+    finally:
+        p.close()

@@ -1,0 +1,62 @@
+"""Host logic of the N-GPU replica run (one process per GPU, independent
+problems), exercised with world size 2 on the gloo backend on CPU: the
+barrier, the maximum of the per-rank times, the whole-job throughput, the
+per-rank seeds, and the reference arm's non-zero ranks exiting without work."""
+
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_2109_10687_gb300 import replicas
+    os.environ.update(WORLD_SIZE=str(world), RANK=str(rank), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        w, r, lr = replicas.rank_env()
+        replicas.barrier(w)
+        elapsed = replicas.max_over_ranks(1.5 + rank, w)          # rank 1 is the slower one
+        value = replicas.job_throughput(w, 4, elapsed)
+        seeds = replicas.replica_seeds(1001, 2001, r)
+        replicas.barrier(w)
+        with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as fh:
+            fh.write(f"{w} {r} {lr} {elapsed} {value} {seeds[0]} {seeds[1]}\n")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_world2_gloo(tmp_path):
+    world = 2
+    mp.start_processes(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    rows = [open(tmp_path / f"rank{r}.txt").read().split() for r in range(world)]
+    for r, row in enumerate(rows):
+        w, rk, lr = int(row[0]), int(row[1]), int(row[2])
+        elapsed, value = float(row[3]), float(row[4])
+        assert (w, rk, lr) == (world, r, r)
+        assert elapsed == 2.5                     # the slowest rank's time on every rank
+        assert value == pytest.approx(2 * 4 / 2.5)  # all ranks' units / max time
+    seeds = {(int(row[5]), int(row[6])) for row in rows}
+    assert len(seeds) == world                    # independent replicas
+
+
+def test_reference_arm_nonzero_rank_exits_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0
+    assert res.stdout.strip() == ""
