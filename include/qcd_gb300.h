@@ -152,7 +152,12 @@ int qcd_build_clover(qcd_ctx* ctx, void* stream);
 /* Bytes of one internal quark field of the given precision times nrhs. */
 int qcd_field_bytes(const qcd_ctx* ctx, int prec, int nrhs, size_t* bytes);
 
-/* Canonical float64 (host or device) -> internal layout of precision prec. */
+/* Canonical float64 (host or device) -> internal layout of precision prec.
+ * A host buffer (src_on_device = 0 / dst_on_device = 0) in page-locked
+ * memory is read or written by the conversion kernel itself through its
+ * mapped device address; pageable memory goes through a temporary device
+ * copy.  With a host buffer both calls return after the transfer is
+ * complete, so the buffer may be reused at once. */
 int qcd_import_spinor(qcd_ctx* ctx, void* dst, const double* src, int prec, int nrhs,
                       int src_on_device, void* stream);
 

@@ -453,6 +453,19 @@ extern "C" int qcd_field_bytes(const qcd_ctx* ctx, int prec, int nrhs, size_t* b
   return QCD_OK;
 }
 
+// Device address through which kernels can read or write a page-locked host
+// buffer directly (mapped pinned memory; null for pageable memory).  Host
+// data in a pinned buffer then crosses the host link once, inside the
+// import or export kernel, with no staging copy in device memory.
+static const void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the (non-sticky) error left by the query
+    return nullptr;
+  }
+  return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
+}
+
 extern "C" int qcd_import_spinor(qcd_ctx* ctx, void* dst, const double* src, int prec, int nrhs,
                                  int src_on_device, void* stream) {
   if (!ctx) return QCD_ERR_ARG;
@@ -465,9 +478,13 @@ extern "C" int qcd_import_spinor(qcd_ctx* ctx, void* dst, const double* src, int
   const double* s = src;
   double* tmp = nullptr;
   if (!src_on_device) {
-    QCD_CUDA_CHECK(cudaMalloc(&tmp, bytes));
-    QCD_CUDA_CHECK(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, st));
-    s = tmp;
+    if (const void* m = mapped_host_ptr(src)) {
+      s = static_cast<const double*>(m);
+    } else {
+      QCD_CUDA_CHECK(cudaMalloc(&tmp, bytes));
+      QCD_CUDA_CHECK(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, st));
+      s = tmp;
+    }
   }
   dim3 grid(grid_for(g.vol, 128), nrhs);
   {
@@ -478,9 +495,9 @@ extern "C" int qcd_import_spinor(qcd_ctx* ctx, void* dst, const double* src, int
     else import_spinor_kernel<QCD_PREC_HALF><<<grid, 128, 0, st>>>(g, dst, s, nrhs, pb);
     check_launch();
   }
-  if (tmp) {
-    QCD_CUDA_CHECK(cudaStreamSynchronize(st));
-    cudaFree(tmp);
+  if (!src_on_device) {
+    QCD_CUDA_CHECK(cudaStreamSynchronize(st));  // the host buffer may be reused on return
+    if (tmp) cudaFree(tmp);
   }
   QCD_API_END(ctx)
 }
@@ -497,8 +514,12 @@ extern "C" int qcd_export_spinor(qcd_ctx* ctx, double* dst, const void* src, int
   double* d = dst;
   double* tmp = nullptr;
   if (!dst_on_device) {
-    QCD_CUDA_CHECK(cudaMalloc(&tmp, bytes));
-    d = tmp;
+    if (const void* m = mapped_host_ptr(dst)) {
+      d = static_cast<double*>(const_cast<void*>(m));
+    } else {
+      QCD_CUDA_CHECK(cudaMalloc(&tmp, bytes));
+      d = tmp;
+    }
   }
   dim3 grid(grid_for(g.vol, 128), nrhs);
   {
@@ -513,6 +534,8 @@ extern "C" int qcd_export_spinor(qcd_ctx* ctx, double* dst, const void* src, int
     QCD_CUDA_CHECK(cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaStreamSynchronize(st));
     cudaFree(tmp);
+  } else if (!dst_on_device) {
+    QCD_CUDA_CHECK(cudaStreamSynchronize(st));  // the host buffer is complete on return
   }
   QCD_API_END(ctx)
 }

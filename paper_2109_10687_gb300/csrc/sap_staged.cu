@@ -344,12 +344,18 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   const int s = threadIdx.x;
   const int dom = a.colour * g.nhalf + blockIdx.x;
 
+  // programmatic dependent launch: the next launch in the stream may start
+  // its CTAs while this grid drains
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (s == 0) {
     mbar_init(bar, 1);
     mbar_expect_tx(bar, ST::LINK_BYTES + ST::CLOV_BYTES);
     bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, bar);
     bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, bar);
   }
+  // the staged links and C_inv are constant during a solve; everything read
+  // below may come from the previous launch, which must be complete
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int r = 0; r < a.nrhs; ++r) {
     const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
     const int rhs_off = r * g.ndom;
@@ -528,7 +534,17 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
       a.x_out32 = last ? x_out32 : F32Spinor{nullptr};
       a.x_store = (!last || !x_out32.p || colour == 0) ? 1 : 0;
       LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
-      sap_staged_kernel<HALF, SIO><<<ctx->geom.nhalf, ST_THREADS, smem, st>>>(a);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(ctx->geom.nhalf);
+      cfg.blockDim = dim3(ST_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      QCD_CUDA_CHECK(cudaLaunchKernelEx(&cfg, sap_staged_kernel<HALF, SIO>, a));
       check_launch();
     }
   }
