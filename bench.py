@@ -399,6 +399,16 @@ def main():
         info_hg = solve(P_HG)
     barrier()
     hg_ms = 1000.0 * (time.perf_counter() - th) / nf
+    # the same float16 SAP-BiCGStab inner solve under a flexible GMRES(4) outer iteration
+    P_FG = params("half")
+    P_FG.outer_restart = 4
+    solve(P_FG)
+    barrier()
+    tg = time.perf_counter()
+    for _ in range(nf):
+        info_fg = solve(P_FG)
+    barrier()
+    fg_ms = 1000.0 * (time.perf_counter() - tg) / nf
 
     # Dslash: float32 D on the 32^4 field, CUDA events on the launching stream
     a32 = lat.field("single")
@@ -466,7 +476,9 @@ def main():
         "plain_fp32": {"time_to_solution_ms": f32_ms, "inner": info_f32.inner_iters, "outer": info_f32.outer_iters,
                        "true_resid": info_f32.true_resid, "speedup_of_mixed": f32_ms / graph_ms},
         "variants_ms": {"f16_all_graph_loop": graph_ms, "f16_links_clover_f32_vectors_graph_loop": hg_ms,
-                        "f32_graph_loop": f32_ms, "f16_all_no_graph_events_per_launch": prof_ms},
+                        "f32_graph_loop": f32_ms, "f16_all_no_graph_events_per_launch": prof_ms,
+                        "f16_all_graph_loop_fgmres4_outer": fg_ms},
+        "fgmres4_outer": {"inner": info_fg.inner_iters, "outer": info_fg.outer_iters, "true_resid": info_fg.true_resid},
         "dslash": {"kernel": "dslash_kernel<float, D>", "ms": d_ms, "gbs": d_gbs, "gflops": d_gflops,
                    "bytes_per_site": D_BYTES_PER_SITE, "flop_per_site": D_FLOP_PER_SITE,
                    "frac_of_hbm": d_gbs / peak, "peak_gbs": peak, "peak_kind": peak_kind},

@@ -95,11 +95,20 @@ typedef struct qcd_solve_params {
   int residual_prec;   /* precision of x, r = b - D x and D in Algorithm 4:
                           1 native float64 (default), 0 double-float (two
                           float32, ~48 bits, on the float32 pipes)           */
+  int outer_restart;   /* outer iteration: 0 (default) the defect correction
+                          of Algorithm 4; m >= 1 flexible GMRES with restart
+                          length m, in float64, each inner SAP-BiCGStab
+                          solve acting as a preconditioner that may change
+                          from step to step (the flexible outer solver Sec. 3
+                          names as an alternative to Algorithm 4; max_outer
+                          then counts its steps).  Requires nrhs = 1 and
+                          residual_prec = 1, else QCD_ERR_ARG.               */
 } qcd_solve_params;
 
 /* Results of qcd_solve, one entry per right-hand side where indicated. */
 typedef struct qcd_solve_info {
-  int outer_iters;         /* defect-correction steps taken                */
+  int outer_iters;         /* outer steps taken (defect-correction or
+                              flexible GMRES steps)                        */
   int inner_iters;         /* BiCGStab iterations summed over outer steps  */
   int status;              /* qcd_status of the solve                      */
   double true_resid;       /* largest final |b - D x| / |b| over the rhs   */

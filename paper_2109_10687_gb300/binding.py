@@ -42,7 +42,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("n_sap", ctypes.c_int), ("n_jac", ctypes.c_int),
                 ("sap_prec", ctypes.c_int), ("use_graph", ctypes.c_int), ("x_is_guess", ctypes.c_int),
-                ("residual_prec", ctypes.c_int)]
+                ("residual_prec", ctypes.c_int), ("outer_restart", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

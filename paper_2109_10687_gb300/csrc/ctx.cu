@@ -101,21 +101,37 @@ __device__ __forceinline__ void paper_to_chiral(cx<double> p[4], cx<double> q[4]
   q[3] = r * (p[1] - p[3]);
 }
 
+// The canonical side of both conversions is moved through shared memory: a
+// block's 128 sites are 24 KB of consecutive canonical data, read or written
+// one double per thread by consecutive threads (the canonical buffer is only
+// guaranteed 8-byte alignment).  Every access is fully coalesced, which
+// matters most when the canonical buffer is page-locked host memory reached
+// over the host link.  An odd row stride (25 doubles per site) keeps the
+// per-site shared-memory accesses free of bank conflicts.
+constexpr int CONV_THREADS = 128;
+constexpr int CONV_STRIDE = 25;
+
 template <int PREC>
-__global__ void import_spinor_kernel(Geom g, void* dst, const double* __restrict__ src, int nrhs,
-                                     int paper_basis) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(CONV_THREADS) import_spinor_kernel(Geom g, void* dst, const double* __restrict__ src,
+                                                                     int nrhs, int paper_basis) {
+  __shared__ double buf[CONV_THREADS * CONV_STRIDE];
+  const long long n0 = blockIdx.x * (long long)CONV_THREADS;
+  const long long n = n0 + threadIdx.x;
   const int rhs = blockIdx.y;
-  if (n >= g.vol || rhs >= nrhs) return;
+  const int nsites = (int)min((long long)CONV_THREADS, g.vol - n0);
+  const double* in = src + ((size_t)rhs * g.vol + n0) * 24;
+  for (int i = threadIdx.x; i < nsites * 24; i += CONV_THREADS) buf[(i / 24) * CONV_STRIDE + i % 24] = in[i];
+  __syncthreads();
+  if (n >= g.vol) return;
   int x[4];
   site_coords(g, n, x);
   int dom, s;
   coords_to_internal(g, x, dom, s);
-  const double* in = src + ((size_t)rhs * g.vol + n) * 24;
+  const double* mine = buf + threadIdx.x * CONV_STRIDE;
   Spinor<double> a;
   for (int c = 0; c < 3; ++c) {
     cx<double> p[4], q[4];
-    for (int sp = 0; sp < 4; ++sp) p[sp] = make_cx(in[(c * 4 + sp) * 2], in[(c * 4 + sp) * 2 + 1]);
+    for (int sp = 0; sp < 4; ++sp) p[sp] = make_cx(mine[(c * 4 + sp) * 2], mine[(c * 4 + sp) * 2 + 1]);
     if (paper_basis) paper_to_chiral(p, q);
     else
       for (int sp = 0; sp < 4; ++sp) q[sp] = p[sp];
@@ -141,45 +157,52 @@ __global__ void import_spinor_kernel(Geom g, void* dst, const double* __restrict
 }
 
 template <int PREC>
-__global__ void export_spinor_kernel(Geom g, double* __restrict__ dst, const void* src, int nrhs,
-                                     int paper_basis) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(CONV_THREADS) export_spinor_kernel(Geom g, double* __restrict__ dst, const void* src,
+                                                                     int nrhs, int paper_basis) {
+  __shared__ double buf[CONV_THREADS * CONV_STRIDE];
+  const long long n0 = blockIdx.x * (long long)CONV_THREADS;
+  const long long n = n0 + threadIdx.x;
   const int rhs = blockIdx.y;
-  if (n >= g.vol || rhs >= nrhs) return;
-  int x[4];
-  site_coords(g, n, x);
-  int dom, s;
-  coords_to_internal(g, x, dom, s);
-  const int domr = dom + rhs * g.ndom;
-  Spinor<double> a;
-  if (PREC == QCD_PREC_DOUBLE) {
-    F64Spinor i{(double2*)src};
-    i.load(g, domr, s, a);
-  } else {
-    Spinor<float> f;
-    if (PREC == QCD_PREC_SINGLE) {
-      F32Spinor i{(float4*)src};
-      i.load(g, domr, s, f);
+  const int nsites = (int)min((long long)CONV_THREADS, g.vol - n0);
+  if (n < g.vol) {
+    int x[4];
+    site_coords(g, n, x);
+    int dom, s;
+    coords_to_internal(g, x, dom, s);
+    const int domr = dom + rhs * g.ndom;
+    Spinor<double> a;
+    if (PREC == QCD_PREC_DOUBLE) {
+      F64Spinor i{(double2*)src};
+      i.load(g, domr, s, a);
     } else {
-      const size_t nv = (size_t)g.vol * nrhs;
-      F16Spinor i{(uint4*)src, (float*)((uint4*)src + 3 * nv)};
-      i.load(g, domr, s, f);
+      Spinor<float> f;
+      if (PREC == QCD_PREC_SINGLE) {
+        F32Spinor i{(float4*)src};
+        i.load(g, domr, s, f);
+      } else {
+        const size_t nv = (size_t)g.vol * nrhs;
+        F16Spinor i{(uint4*)src, (float*)((uint4*)src + 3 * nv)};
+        i.load(g, domr, s, f);
+      }
+      for (int sp = 0; sp < 4; ++sp)
+        for (int c = 0; c < 3; ++c) a.v[sp][c] = make_cx((double)f.v[sp][c].re, (double)f.v[sp][c].im);
     }
-    for (int sp = 0; sp < 4; ++sp)
-      for (int c = 0; c < 3; ++c) a.v[sp][c] = make_cx((double)f.v[sp][c].re, (double)f.v[sp][c].im);
-  }
-  double* out = dst + ((size_t)rhs * g.vol + n) * 24;
-  for (int c = 0; c < 3; ++c) {
-    cx<double> p[4], q[4];
-    for (int sp = 0; sp < 4; ++sp) p[sp] = a.v[sp][c];
-    if (paper_basis) paper_to_chiral(p, q);  // S is its own inverse
-    else
-      for (int sp = 0; sp < 4; ++sp) q[sp] = p[sp];
-    for (int sp = 0; sp < 4; ++sp) {
-      out[(c * 4 + sp) * 2] = q[sp].re;
-      out[(c * 4 + sp) * 2 + 1] = q[sp].im;
+    double* mine = buf + threadIdx.x * CONV_STRIDE;
+    for (int c = 0; c < 3; ++c) {
+      cx<double> p[4], q[4];
+      for (int sp = 0; sp < 4; ++sp) p[sp] = a.v[sp][c];
+      if (paper_basis) paper_to_chiral(p, q);  // S is its own inverse
+      else
+        for (int sp = 0; sp < 4; ++sp) q[sp] = p[sp];
+      for (int sp = 0; sp < 4; ++sp) {
+        mine[(c * 4 + sp) * 2] = q[sp].re;
+        mine[(c * 4 + sp) * 2 + 1] = q[sp].im;
+      }
     }
   }
+  __syncthreads();
+  double* out = dst + ((size_t)rhs * g.vol + n0) * 24;
+  for (int i = threadIdx.x; i < nsites * 24; i += CONV_THREADS) out[i] = buf[(i / 24) * CONV_STRIDE + i % 24];
 }
 
 // canonical gauge field -> internal float64 / float32 / float16 links, with
@@ -486,13 +509,16 @@ extern "C" int qcd_import_spinor(qcd_ctx* ctx, void* dst, const double* src, int
       s = tmp;
     }
   }
-  dim3 grid(grid_for(g.vol, 128), nrhs);
+  dim3 grid(grid_for(g.vol, CONV_THREADS), nrhs);
   {
     LaunchScope ls(ctx, QCD_KC_OTHER, st);
     const int pb = ctx->basis == QCD_BASIS_PAPER;
-    if (prec == QCD_PREC_DOUBLE) import_spinor_kernel<QCD_PREC_DOUBLE><<<grid, 128, 0, st>>>(g, dst, s, nrhs, pb);
-    else if (prec == QCD_PREC_SINGLE) import_spinor_kernel<QCD_PREC_SINGLE><<<grid, 128, 0, st>>>(g, dst, s, nrhs, pb);
-    else import_spinor_kernel<QCD_PREC_HALF><<<grid, 128, 0, st>>>(g, dst, s, nrhs, pb);
+    if (prec == QCD_PREC_DOUBLE)
+      import_spinor_kernel<QCD_PREC_DOUBLE><<<grid, CONV_THREADS, 0, st>>>(g, dst, s, nrhs, pb);
+    else if (prec == QCD_PREC_SINGLE)
+      import_spinor_kernel<QCD_PREC_SINGLE><<<grid, CONV_THREADS, 0, st>>>(g, dst, s, nrhs, pb);
+    else
+      import_spinor_kernel<QCD_PREC_HALF><<<grid, CONV_THREADS, 0, st>>>(g, dst, s, nrhs, pb);
     check_launch();
   }
   if (!src_on_device) {
@@ -521,13 +547,16 @@ extern "C" int qcd_export_spinor(qcd_ctx* ctx, double* dst, const void* src, int
       d = tmp;
     }
   }
-  dim3 grid(grid_for(g.vol, 128), nrhs);
+  dim3 grid(grid_for(g.vol, CONV_THREADS), nrhs);
   {
     LaunchScope ls(ctx, QCD_KC_OTHER, st);
     const int pb = ctx->basis == QCD_BASIS_PAPER;
-    if (prec == QCD_PREC_DOUBLE) export_spinor_kernel<QCD_PREC_DOUBLE><<<grid, 128, 0, st>>>(g, d, src, nrhs, pb);
-    else if (prec == QCD_PREC_SINGLE) export_spinor_kernel<QCD_PREC_SINGLE><<<grid, 128, 0, st>>>(g, d, src, nrhs, pb);
-    else export_spinor_kernel<QCD_PREC_HALF><<<grid, 128, 0, st>>>(g, d, src, nrhs, pb);
+    if (prec == QCD_PREC_DOUBLE)
+      export_spinor_kernel<QCD_PREC_DOUBLE><<<grid, CONV_THREADS, 0, st>>>(g, d, src, nrhs, pb);
+    else if (prec == QCD_PREC_SINGLE)
+      export_spinor_kernel<QCD_PREC_SINGLE><<<grid, CONV_THREADS, 0, st>>>(g, d, src, nrhs, pb);
+    else
+      export_spinor_kernel<QCD_PREC_HALF><<<grid, CONV_THREADS, 0, st>>>(g, d, src, nrhs, pb);
     check_launch();
   }
   if (tmp) {

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <complex>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -58,6 +59,11 @@ struct Workspace {
   int* ctrl = nullptr;     // device: [0] rhs still iterating, [1] iterations, [2] iteration limit
   int* h_ctrl = nullptr;   // pinned
   int nblocks = 0;
+  // flexible GMRES: basis V (m + 1 vectors), preconditioned directions Z
+  // (m vectors), float64 internal layout, and its Hessenberg column scratch
+  double2* fg = nullptr;
+  double* fg_h = nullptr;
+  int fg_m = 0;
   // instantiated CUDA graphs of the inner loop, reused while the key matches
   struct Graphs {
     int nrhs = -1, n_sap = -1, n_jac = -1, sap_prec = -1, mode = -1;
@@ -81,6 +87,8 @@ void workspace_free(qcd_ctx* ctx) {
                   w->x64, w->r64, w->b64, w->t64, w->partials, w->dres, w->counters, w->scal};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (w->fg) cudaFree(w->fg);
+  if (w->fg_h) cudaFree(w->fg_h);
   if (w->h_scal) cudaFreeHost(w->h_scal);
   if (w->h_red) cudaFreeHost(w->h_red);
   if (w->ctrl) cudaFree(w->ctrl);
@@ -450,6 +458,69 @@ __global__ void k_residual_f64(const double2* __restrict__ b, double2* r, size_t
   if (grid_reduce<1>(v, part, counters + rhs, tot) && threadIdx.x == 0) out[rhs] = tot[0];
 }
 
+// ---------------------------------------------------------------------------
+// float64 vector kernels of the flexible GMRES outer solver (one right-hand
+// side; a vector is n2 complex numbers in the internal float64 layout, whose
+// inner product does not depend on the site order)
+// ---------------------------------------------------------------------------
+// <a|b> = sum conj(a) b -> out[0] (re), out[1] (im)
+__global__ void k_cdot_f64(const double2* __restrict__ a, const double2* __restrict__ b, size_t n2, double* out,
+                           double* partials, unsigned* counters) {
+  double re = 0.0, im = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 u = a[i], v = b[i];
+    re = fma(u.x, v.x, fma(u.y, v.y, re));
+    im = fma(u.x, v.y, fma(-u.y, v.x, im));
+  }
+  double v[2] = {re, im}, tot[2];
+  if (grid_reduce<2>(v, partials, counters, tot) && threadIdx.x == 0) {
+    out[0] = tot[0];
+    out[1] = tot[1];
+  }
+}
+
+// y -= s x with the complex s = (s[0], s[1]) read from device memory
+__global__ void k_caxmy_f64(double2* y, const double2* __restrict__ x, size_t n2, const double* s) {
+  const double sr = s[0], si = s[1];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 u = x[i];
+    double2 v = y[i];
+    v.x -= sr * u.x - si * u.y;
+    v.y -= sr * u.y + si * u.x;
+    y[i] = v;
+  }
+}
+
+// y += (sr + i si) x, scalar from the host
+__global__ void k_caxpy_f64(double2* y, const double2* __restrict__ x, size_t n2, double sr, double si) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 u = x[i];
+    double2 v = y[i];
+    v.x += sr * u.x - si * u.y;
+    v.y += sr * u.y + si * u.x;
+    y[i] = v;
+  }
+}
+
+// v *= f with f = 1 / sqrt(n2[0]) read from device memory (v / |v|); no-op for a zero norm
+__global__ void k_normalize_f64(double2* v, size_t n2, const double* norm2) {
+  const double q = norm2[0];
+  if (!(q > 0.0)) return;
+  const double f = 1.0 / sqrt(q);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 u = v[i];
+    v[i] = make_double2(u.x * f, u.y * f);
+  }
+}
+
+// v = f w (real f from the host)
+__global__ void k_scale_f64(double2* v, const double2* __restrict__ w, size_t n2, double f) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 u = w[i];
+    v[i] = make_double2(u.x * f, u.y * f);
+  }
+}
+
 // float32 p = R_SP(r / err): same internal site order, float64 complex ->
 // float32 pairs (the float64 and float32 layouts order components alike
 // within a domain: float4 group k holds complex components 2k, 2k+1)
@@ -806,6 +877,7 @@ extern "C" int qcd_solve_params_default(qcd_solve_params* p) {
   p->use_graph = 0;
   p->x_is_guess = 0;
   p->residual_prec = 1;
+  p->outer_restart = 0;
   return QCD_OK;
 }
 
@@ -923,6 +995,9 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
               QCD_ERR_ARG, "qcd_solve: bad parameters");
   QCD_REQUIRE(P.sap_prec == QCD_PREC_SINGLE || P.sap_prec == QCD_PREC_HALF || P.sap_prec == QCD_PREC_HALF_GAUGE,
               QCD_ERR_ARG, "qcd_solve: sap_prec must be SINGLE, HALF or HALF_GAUGE");
+  QCD_REQUIRE(P.outer_restart >= 0 && P.outer_restart <= 64, QCD_ERR_ARG, "qcd_solve: outer_restart in [0, 64]");
+  QCD_REQUIRE(P.outer_restart == 0 || (nrhs == 1 && P.residual_prec == 1), QCD_ERR_ARG,
+              "qcd_solve: flexible GMRES needs nrhs = 1 and residual_prec = 1");
   cudaStream_t st = (cudaStream_t)stream;
   if (P.use_graph) {
     // stream capture is not possible on the legacy default stream: run the
@@ -1001,6 +1076,143 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   int outer = 0, inner_total = 0, last_inner_status = QCD_OK, breakdowns = 0;
   double worst_rel = 0.0;
   auto rel = [&](int r) { return h_b2[r] > 0 ? std::sqrt(h_r2[r] / h_b2[r]) : 0.0; };
+  if (P.outer_restart > 0) {
+    // ---- flexible GMRES(m) in float64 (one right-hand side) ----------------
+    // Arnoldi on D with the inner SAP-BiCGStab solve z_j ~ D^-1 v_j as a
+    // preconditioner that may differ from step to step, so the directions
+    // z_j are kept and x += Z y at the end of each cycle; modified
+    // Gram-Schmidt in float64; complex Givens rotations on the host give the
+    // residual estimate |g_{j+1}| after every step.  Each cycle ends with
+    // the true residual r = b - D x.
+    using cplx = std::complex<double>;
+    const int m = P.outer_restart;
+    if (w->fg_m < m) {
+      if (w->fg) cudaFree(w->fg);
+      if (w->fg_h) cudaFree(w->fg_h);
+      w->fg = nullptr;
+      w->fg_h = nullptr;
+      w->fg_m = 0;
+      QCD_CUDA_CHECK(cudaMalloc(&w->fg, sizeof(double2) * n2 * (2 * (size_t)m + 1)));
+      QCD_CUDA_CHECK(cudaMalloc(&w->fg_h, sizeof(double) * 2 * (m + 2)));
+      w->fg_m = m;
+    }
+    double2* V = w->fg;                        // v_i = V + i n2, i = 0..m
+    double2* Z = w->fg + (size_t)(m + 1) * n2;  // z_j = Z + j n2, j < m
+    const dim3 vgrid(w->nblocks, 1);
+    std::vector<cplx> H((size_t)(m + 1) * m), sn(m), gv(m + 1), y(m);
+    std::vector<double> cs(m), hcol(2 * (m + 2));
+    const double bnorm = std::sqrt(h_b2[0]);
+    h_scale[0] = 1.0;
+    QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double), cudaMemcpyHostToDevice, st));
+    bool stop = false;
+    while (!stop) {
+      worst_rel = rel(0);
+      if (!std::isfinite(h_r2[0])) {
+        result = QCD_ERR_NONFINITE;
+        break;
+      }
+      if (worst_rel < P.tol) break;
+      if (outer >= P.max_outer) {
+        result = last_inner_status == QCD_ERR_BREAKDOWN ? QCD_ERR_BREAKDOWN : QCD_ERR_NOT_CONVERGED;
+        break;
+      }
+      const double beta = std::sqrt(h_r2[0]);
+      {
+        LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+        k_scale_f64<<<vgrid, RED_THREADS, 0, st>>>(V, w->r64, n2, 1.0 / beta);
+        check_launch();
+      }
+      std::fill(gv.begin(), gv.end(), cplx(0.0));
+      gv[0] = beta;
+      int j = 0;
+      while (j < m && outer < P.max_outer) {
+        ++outer;
+        double2* vj = V + (size_t)j * n2;
+        double2* vn = V + (size_t)(j + 1) * n2;
+        double2* zj = Z + (size_t)j * n2;
+        // z_j: the inner solve of A q = C_inv R_SP(v_j), i.e. D q = v_j
+        {
+          LaunchScope ls(ctx, QCD_KC_BLAS, st);
+          k_f64_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, vj, w->tmp32, d_red + 2 * nrhs);
+          check_launch();
+        }
+        clover_apply_launch(ctx, w->tmp32, w->tmp32, QCD_PREC_SINGLE, 1, 1, st);
+        int st_inner = QCD_OK;
+        inner_total += bicgstab_sap(ctx, w, w->tmp32, 1, P, st, &st_inner);
+        last_inner_status = st_inner;
+        if (st_inner == QCD_ERR_BREAKDOWN) ++breakdowns;
+        if (st_inner == QCD_ERR_NONFINITE) {
+          result = QCD_ERR_NONFINITE;
+          stop = true;
+          break;
+        }
+        QCD_CUDA_CHECK(cudaMemsetAsync(zj, 0, sizeof(double2) * n2, st));
+        {
+          LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+          k_f64_axpy_f32<<<sgrid, 128, 0, st>>>(g, zj, w->x, d_red + 2 * nrhs);
+          check_launch();
+        }
+        // v_{j+1} = D z_j orthogonalised against v_0 .. v_j, then normalised
+        dslash_launch(ctx, vn, zj, QCD_PREC_DOUBLE, MODE_D, 1, st);
+        {
+          LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+          for (int i = 0; i <= j; ++i) {
+            const double2* vi = V + (size_t)i * n2;
+            k_cdot_f64<<<vgrid, RED_THREADS, 0, st>>>(vi, vn, n2, w->fg_h + 2 * i, w->partials, w->counters);
+            k_caxmy_f64<<<vgrid, RED_THREADS, 0, st>>>(vn, vi, n2, w->fg_h + 2 * i);
+          }
+          k_norm2_f64<<<vgrid, RED_THREADS, 0, st>>>(vn, n2, w->fg_h + 2 * (j + 1), w->partials, w->counters);
+          k_normalize_f64<<<vgrid, RED_THREADS, 0, st>>>(vn, n2, w->fg_h + 2 * (j + 1));
+          check_launch();
+          ctx->launches += 2 * j + 3;  // 2 (j + 1) + 2 kernels in this scope
+        }
+        QCD_CUDA_CHECK(cudaMemcpyAsync(hcol.data(), w->fg_h, sizeof(double) * 2 * (j + 2), cudaMemcpyDeviceToHost, st));
+        QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cplx(hcol[2 * i], hcol[2 * i + 1]);
+        const double hn = std::sqrt(std::max(hcol[2 * (j + 1)], 0.0));
+        // earlier rotations on column j, then the one that zeroes H[j+1][j]
+        for (int i = 0; i < j; ++i) {
+          const cplx a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+          H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * a + cs[i] * b;
+        }
+        const cplx a = H[(size_t)j * m + j];
+        const double nu = std::sqrt(std::norm(a) + hn * hn);
+        if (std::abs(a) == 0.0) {
+          cs[j] = 0.0;
+          sn[j] = 1.0;
+        } else {
+          cs[j] = std::abs(a) / nu;
+          sn[j] = (a / std::abs(a)) * hn / nu;
+        }
+        H[(size_t)j * m + j] = cs[j] * a + sn[j] * hn;
+        gv[j + 1] = -std::conj(sn[j]) * gv[j];
+        gv[j] = cs[j] * gv[j];
+        ++j;
+        if (!std::isfinite(std::abs(gv[j]))) {
+          result = QCD_ERR_NONFINITE;
+          stop = true;
+          break;
+        }
+        if (std::abs(gv[j]) < P.tol * bnorm || hn == 0.0) break;
+      }
+      if (stop || j == 0) break;
+      // y from the triangular system R y = g, then x += Z y
+      for (int k = j - 1; k >= 0; --k) {
+        cplx acc = gv[k];
+        for (int l = k + 1; l < j; ++l) acc -= H[(size_t)k * m + l] * y[l];
+        y[k] = acc / H[(size_t)k * m + k];
+      }
+      {
+        LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
+        for (int k = 0; k < j; ++k)
+          k_caxpy_f64<<<vgrid, RED_THREADS, 0, st>>>(w->x64, Z + (size_t)k * n2, n2, y[k].real(), y[k].imag());
+        check_launch();
+        ctx->launches += j - 1;
+      }
+      residual();
+    }
+  } else {
   for (;;) {
     worst_rel = 0.0;
     bool finite = true;
@@ -1046,6 +1258,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
       check_launch();
     }
     residual();
+  }
   }
   if (df) {
     LaunchScope ls(ctx, QCD_KC_DOUBLE, st);

@@ -51,3 +51,17 @@ def test_solve_defaults_match_header(lib):
     binding._lib = None
     p = binding.qcd_solve_params_default()
     assert (p.tol, p.inner_tol, p.max_outer, p.max_inner, p.n_sap, p.n_jac) == (1e-10, 1e-6, 20, 500, 4, 4)
+
+
+def test_solve_params_layout_matches_header():
+    """The ctypes mirror of qcd_solve_params lists the header's fields in the
+    header's order with the header's C types."""
+    import re
+    from paper_2109_10687_gb300 import binding
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct qcd_solve_params \{(.*?)\} qcd_solve_params;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(double|int)\s+([A-Za-z0-9_]+)\s*;", body)
+    ctypes_map = {"double": "c_double", "int": "c_int"}
+    got = [(name, t.__name__) for name, t in binding.SolveParams._fields_]
+    assert got == [(name, ctypes_map[t]) for t, name in fields]

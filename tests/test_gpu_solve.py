@@ -164,3 +164,35 @@ def test_solve_full_size_sampled_32x4():
         assert np.sqrt(num / den) < 1e-8
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("sap_prec", ["single", "half"])
+def test_fgmres_outer_to_1e10(c1, c1_ref, sap_prec):
+    """Flexible GMRES(4) as the outer iteration, the inner SAP-BiCGStab solve
+    as its varying preconditioner: same true residual and solution bars as
+    the defect correction of Algorithm 4."""
+    b, x_ref = c1_ref
+    x, rc, info = c1.lat.solve(b, tol=1e-10, inner_tol=1e-5, sap_prec=sap_prec, outer_restart=4, use_graph=2)
+    x = to_np(x)
+    assert rc == 0 and info.true_resid < 1e-10
+    assert true_resid(c1.op, x, b) < 1e-10
+    assert rel_l2(x, x_ref) < 1e-8
+
+
+def test_fgmres_needs_no_more_outer_steps_than_defect_correction(c1, c1_ref):
+    """With a loose inner tolerance the defect correction restarts from the
+    bare residual every step, while flexible GMRES combines all earlier
+    directions: it takes at most as many outer steps."""
+    b, _ = c1_ref
+    _, rc_d, info_d = c1.lat.solve(b, tol=1e-10, inner_tol=1e-2, sap_prec="single", max_outer=60)
+    _, rc_f, info_f = c1.lat.solve(b, tol=1e-10, inner_tol=1e-2, sap_prec="single", max_outer=60, outer_restart=16)
+    assert rc_d == 0 and rc_f == 0
+    assert info_f.true_resid < 1e-10
+    assert info_f.outer_iters <= info_d.outer_iters
+
+
+def test_fgmres_rejects_multi_rhs(c1):
+    from paper_2109_10687_gb300 import binding as B
+    srcs = np.stack([point_source(c1.dims, 0, 0), point_source(c1.dims, 1, 1)])
+    _, rc, _ = c1.lat.solve(srcs, nrhs=2, outer_restart=4, raise_on_error=False)
+    assert rc == B.QCD_ERR_ARG
