@@ -18,6 +18,8 @@ struct qcd_batch {
   qcd::BatchDesc* d_desc = nullptr;
   qcd::BatchDesc* h_desc = nullptr;  // pinned staging of the descriptors
   cudaEvent_t desc_free = nullptr;   // the previous descriptor copy has completed
+  int* d_block_lat = nullptr;        // lattice of every block of the one-launch D
+  long long nblocks = 0;
   std::string err;
 };
 
@@ -57,6 +59,7 @@ extern "C" int qcd_batch_destroy(qcd_batch* b) {
   if (b->d_desc) cudaFree(b->d_desc);
   if (b->h_desc) cudaFreeHost(b->h_desc);
   if (b->desc_free) cudaEventDestroy(b->desc_free);
+  if (b->d_block_lat) cudaFree(b->d_block_lat);
   delete b;
   return QCD_OK;
 }
@@ -86,11 +89,23 @@ extern "C" int qcd_batch_apply_D(qcd_batch* b, void* const* out, const void* con
       d.block_begin = blocks;
       blocks += (c->geom.vol + 127) / 128;
     }
+    if (!b->d_block_lat) {
+      // the geometries are fixed for the batch's lifetime: build the table once
+      std::vector<int> lat((size_t)blocks);
+      for (int i = 0; i < n; ++i) {
+        const long long end = i + 1 < n ? b->h_desc[i + 1].block_begin : blocks;
+        for (long long k = b->h_desc[i].block_begin; k < end; ++k) lat[(size_t)k] = i;
+      }
+      QCD_CUDA_CHECK(cudaMalloc(&b->d_block_lat, sizeof(int) * lat.size()));
+      QCD_CUDA_CHECK(cudaMemcpy(b->d_block_lat, lat.data(), sizeof(int) * lat.size(), cudaMemcpyHostToDevice));
+      b->nblocks = blocks;
+    }
+    QCD_REQUIRE(b->nblocks == blocks, QCD_ERR_STATE, "qcd_batch_apply_D: lattice sizes changed");
     QCD_CUDA_CHECK(cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, st));
     QCD_CUDA_CHECK(cudaEventRecord(b->desc_free, st));
     {
       LaunchScope ls(b->ctx[0], QCD_KC_DSLASH, st);
-      dslash_batch_launch(b->d_desc, n, blocks, dagger, st);
+      dslash_batch_launch(b->d_desc, b->d_block_lat, blocks, dagger, st);
     }
   } catch (const qcd::Error& e) {
     b->err = e.msg;

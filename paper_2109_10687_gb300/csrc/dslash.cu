@@ -206,23 +206,33 @@ __global__ void __launch_bounds__(THREADS, MINB)
 }
 
 // Ragged batch: one launch over several lattices of different sizes.  Block
-// b belongs to the lattice whose [block_begin, block_end) range holds it.
-__global__ void __launch_bounds__(128, 4) dslash_batch_kernel(const BatchDesc* __restrict__ desc, int n, int dagger) {
-  int i = 0;
-  while (i + 1 < n && (long long)blockIdx.x >= desc[i + 1].block_begin) ++i;
-  const BatchDesc& d = desc[i];
-  const long long gid = ((long long)blockIdx.x - d.block_begin) * 128 + threadIdx.x;
-  if (gid >= d.g.vol) return;
-  const F32Spinor out{d.out}, in{(float4*)d.in};
-  const LinkPtr<float> U{d.u};
-  const CloverPtrF32 clov{d.clov};
-  if (dagger) dslash_site<float, MODE_DDAG>(d.g, out, in, U, clov, d.kappa, gid, 0);
-  else dslash_site<float, MODE_D>(d.g, out, in, U, clov, d.kappa, gid, 0);
+// b belongs to lattice block_lat[b] (a table built once per batch); the
+// block copies that lattice's descriptor (geometry, field pointers, kappa)
+// to shared memory, so the geometry is read from there rather than from
+// global memory on every index computation.
+__global__ void __launch_bounds__(128, 4) dslash_batch_kernel(const BatchDesc* __restrict__ desc,
+                                                              const int* __restrict__ block_lat, int dagger) {
+  __shared__ BatchDesc sd;
+  {
+    const int i = __ldg(block_lat + blockIdx.x);
+    const int* src = reinterpret_cast<const int*>(desc + i);
+    int* dst = reinterpret_cast<int*>(&sd);
+    for (int k = threadIdx.x; k < (int)(sizeof(BatchDesc) / sizeof(int)); k += blockDim.x) dst[k] = __ldg(src + k);
+  }
+  __syncthreads();
+  const long long gid = ((long long)blockIdx.x - sd.block_begin) * 128 + threadIdx.x;
+  if (gid >= sd.g.vol) return;
+  const F32Spinor out{sd.out}, in{(float4*)sd.in};
+  const LinkPtr<float> U{sd.u};
+  const CloverPtrF32 clov{sd.clov};
+  if (dagger) dslash_site<float, MODE_DDAG, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
+  else dslash_site<float, MODE_D, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
 }
 
-void dslash_batch_launch(const BatchDesc* d_desc, int n, long long total_blocks, int dagger, cudaStream_t st) {
+void dslash_batch_launch(const BatchDesc* d_desc, const int* d_block_lat, long long total_blocks, int dagger,
+                         cudaStream_t st) {
   QCD_REQUIRE(total_blocks < (1LL << 31), QCD_ERR_ARG, "batch too large for one launch");
-  dslash_batch_kernel<<<(unsigned)total_blocks, 128, 0, st>>>(d_desc, n, dagger);
+  dslash_batch_kernel<<<(unsigned)total_blocks, 128, 0, st>>>(d_desc, d_block_lat, dagger);
   check_launch();
 }
 
@@ -293,6 +303,20 @@ static void launch_dslash_f32(int variant, const Geom& g, void* out, const void*
     default: launch_dslash_shape<float, MODE, 256, 2, true>(g, out, in, U, clov, kappa, nrhs, st); break;
   }
 }
+// float64 launch shapes (register budget against resident warps)
+template <int MODE>
+static void launch_dslash_f64(int variant, const Geom& g, void* out, const void* in, const void* U, const void* clov,
+                              double kappa, int nrhs, cudaStream_t st) {
+  switch (variant) {
+    case 0: launch_dslash_shape<double, MODE, 128, 1>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 1: launch_dslash_shape<double, MODE, 128, 2>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 2: launch_dslash_shape<double, MODE, 128, 3>(g, out, in, U, clov, kappa, nrhs, st); break;
+    default: launch_dslash_shape<double, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st); break;
+  }
+}
+static const char* kDslashShapes64[] = {"128x1", "128x2", "128x3", "128x4"};
+constexpr int kNumDslashShapes64 = 4;
+
 static const char* kDslashShapes[] = {"128x4", "128x5", "128x6", "256x2", "128x4h", "128x5h", "128x6h", "256x2h"};
 constexpr int kNumDslashShapes = 8;
 
@@ -310,12 +334,16 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
     check_launch();
   } else if (prec == QCD_PREC_DOUBLE) {
     QCD_REQUIRE(mode != MODE_A, QCD_ERR_ARG, "A is provided in float32 only");
+    auto run = [&](int v) {
+      if (mode == MODE_D) launch_dslash_f64<MODE_D>(v, g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
+      else launch_dslash_f64<MODE_DDAG>(v, g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
+      check_launch();
+    };
+    char key[64];
+    std::snprintf(key, sizeof key, "dslash_f64_mode%d_nrhs%d", mode, nrhs);
+    const int v = tune_pick(ctx, key, kNumDslashShapes64, kDslashShapes64, run, st);
     LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-    if (mode == MODE_D)
-      launch_dslash_shape<double, MODE_D, 128, 1>(g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
-    else
-      launch_dslash_shape<double, MODE_DDAG, 128, 1>(g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
-    check_launch();
+    run(v);
   } else if (prec == QCD_PREC_SINGLE) {
     const float k = (float)ctx->kappa;
     const void* clov = mode == MODE_A ? (const void*)ctx->cinv32 : (const void*)ctx->clov32;

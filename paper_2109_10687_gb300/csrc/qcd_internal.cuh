@@ -727,6 +727,7 @@ struct BatchDesc {
   float kappa;
   long long block_begin;  // first block of this lattice in the batched launch
 };
-void dslash_batch_launch(const BatchDesc* d_desc, int n, long long total_blocks, int dagger, cudaStream_t st);
+void dslash_batch_launch(const BatchDesc* d_desc, const int* d_block_lat, long long total_blocks, int dagger,
+                         cudaStream_t st);
 
 }  // namespace qcd
