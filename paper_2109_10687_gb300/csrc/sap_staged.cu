@@ -27,6 +27,7 @@ namespace qcd {
 
 constexpr int ST_THREADS = 256;
 constexpr int C16_U4 = 11;   // uint4 per site, f16 C_inv
+constexpr int L16_H2 = 10;   // half2 per link, f16 links (9 + 1 pad)
 constexpr int C32_F4 = 19;   // float4 per site, f32 C_inv
 
 template <bool HALF>
@@ -34,16 +35,23 @@ struct StageT;
 
 template <>
 struct StageT<true> {
-  static constexpr int LINK_BYTES = 4 * 256 * 9 * 4;       // 36864
+  static constexpr int LINK_BYTES = 4 * 256 * L16_H2 * 4;  // 40960
   static constexpr int CLOV_BYTES = 256 * C16_U4 * 16;     // 45056
   using SIO = F16Spinor;
+  // a link is 9 half2 padded to 10 (40 bytes): five 8-byte reads, and the
+  // 10-word site stride keeps a half warp's 8-byte reads on distinct banks
   __device__ static SU3<float> link(const unsigned char* base, int mu, int site) {
-    const __half2* p = reinterpret_cast<const __half2*>(base) + (mu * 256 + site) * 9;
+    const uint2* p = reinterpret_cast<const uint2*>(base) + (mu * 256 + site) * (L16_H2 / 2);
     SU3<float> u;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      const float2 v = __half22float2(p[e]);
-      u.m[e / 3][e % 3] = make_cx(v.x, v.y);
+    for (int k = 0; k < 5; ++k) {
+      const uint2 w = p[k];
+      const float2 v0 = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+      u.m[(2 * k) / 3][(2 * k) % 3] = make_cx(v0.x, v0.y);
+      if (2 * k + 1 < 9) {
+        const float2 v1 = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+        u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v1.x, v1.y);
+      }
     }
     return u;
   }
@@ -447,9 +455,10 @@ __global__ void build_link_stage_kernel(Geom g, const double2* u64, __half2* l16
   for (int e = 0; e < 9; ++e) {
     const double2 v = u64[(((size_t)((dom * 4 + mu) * 9 + e)) << 8) + s];
     const size_t o = ((size_t)(dom * 4 + mu) * 256 + s) * 9 + e;
-    l16[o] = __floats2half2_rn((float)v.x, (float)v.y);
+    l16[((size_t)(dom * 4 + mu) * 256 + s) * L16_H2 + e] = __floats2half2_rn((float)v.x, (float)v.y);
     l32[o] = make_float2((float)v.x, (float)v.y);
   }
+  l16[((size_t)(dom * 4 + mu) * 256 + s) * L16_H2 + 9] = __floats2half2_rn(0.f, 0.f);
 }
 
 __global__ void build_clover_stage_kernel(Geom g, const double2* c64, uint4* c16, float4* c32) {
