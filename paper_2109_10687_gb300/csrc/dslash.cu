@@ -201,6 +201,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
                   typename Prec<R>::CP clov, R kappa, int nrhs) {
   const int rhs = blockIdx.x % nrhs;
   const long long gid = (blockIdx.x / nrhs) * (long long)THREADS + threadIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (gid >= g.vol || loop_idle(g)) return;
   dslash_site<R, MODE, HINT>(g, out, in, U, clov, kappa, gid, rhs);
 }
@@ -279,39 +281,44 @@ __global__ void __launch_bounds__(128) ablock_kernel(Geom g, F32Spinor out, F32S
 
 template <typename R, int MODE, int THREADS, int MINB, bool HINT = false>
 static void launch_dslash_shape(const Geom& g, void* out, const void* in, const void* U, const void* clov, R kappa,
-                                int nrhs, cudaStream_t st) {
+                                int nrhs, cudaStream_t st, bool pdl) {
   using P = Prec<R>;
   const long long blocks = (long long)grid_for(g.vol, THREADS) * nrhs;
   QCD_REQUIRE(blocks < (1LL << 31), QCD_ERR_ARG, "lattice too large for one launch");
-  dslash_kernel<R, MODE, THREADS, MINB, HINT><<<(unsigned)blocks, THREADS, 0, st>>>(
-      g, typename P::SIO{(decltype(P::SIO::p))out}, typename P::SIO{(decltype(P::SIO::p))in},
-      typename P::LP{(decltype(P::LP::p))U}, typename P::CP{(decltype(P::CP::p))clov}, kappa, nrhs);
+  const typename P::SIO o{(decltype(P::SIO::p))out}, i{(decltype(P::SIO::p))in};
+  const typename P::LP u{(decltype(P::LP::p))U};
+  const typename P::CP c{(decltype(P::CP::p))clov};
+  if (pdl)
+    launch_pdl(dslash_kernel<R, MODE, THREADS, MINB, HINT>, dim3((unsigned)blocks), dim3(THREADS), 0, st, g, o, i, u, c,
+               kappa, nrhs);
+  else
+    dslash_kernel<R, MODE, THREADS, MINB, HINT><<<(unsigned)blocks, THREADS, 0, st>>>(g, o, i, u, c, kappa, nrhs);
 }
 
 // float32 launch shapes the autotuner chooses from
 template <int MODE>
 static void launch_dslash_f32(int variant, const Geom& g, void* out, const void* in, const void* U, const void* clov,
-                              float kappa, int nrhs, cudaStream_t st) {
+                              float kappa, int nrhs, cudaStream_t st, bool pdl) {
   switch (variant) {
-    case 0: launch_dslash_shape<float, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 1: launch_dslash_shape<float, MODE, 128, 5>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 2: launch_dslash_shape<float, MODE, 128, 6>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 3: launch_dslash_shape<float, MODE, 256, 2>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 4: launch_dslash_shape<float, MODE, 128, 4, true>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 5: launch_dslash_shape<float, MODE, 128, 5, true>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 6: launch_dslash_shape<float, MODE, 128, 6, true>(g, out, in, U, clov, kappa, nrhs, st); break;
-    default: launch_dslash_shape<float, MODE, 256, 2, true>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 0: launch_dslash_shape<float, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 1: launch_dslash_shape<float, MODE, 128, 5>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 2: launch_dslash_shape<float, MODE, 128, 6>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 3: launch_dslash_shape<float, MODE, 256, 2>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 4: launch_dslash_shape<float, MODE, 128, 4, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 5: launch_dslash_shape<float, MODE, 128, 5, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 6: launch_dslash_shape<float, MODE, 128, 6, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    default: launch_dslash_shape<float, MODE, 256, 2, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
   }
 }
 // float64 launch shapes (register budget against resident warps)
 template <int MODE>
 static void launch_dslash_f64(int variant, const Geom& g, void* out, const void* in, const void* U, const void* clov,
-                              double kappa, int nrhs, cudaStream_t st) {
+                              double kappa, int nrhs, cudaStream_t st, bool pdl) {
   switch (variant) {
-    case 0: launch_dslash_shape<double, MODE, 128, 1>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 1: launch_dslash_shape<double, MODE, 128, 2>(g, out, in, U, clov, kappa, nrhs, st); break;
-    case 2: launch_dslash_shape<double, MODE, 128, 3>(g, out, in, U, clov, kappa, nrhs, st); break;
-    default: launch_dslash_shape<double, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st); break;
+    case 0: launch_dslash_shape<double, MODE, 128, 1>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 1: launch_dslash_shape<double, MODE, 128, 2>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 2: launch_dslash_shape<double, MODE, 128, 3>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    default: launch_dslash_shape<double, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
   }
 }
 static const char* kDslashShapes64[] = {"128x1", "128x2", "128x3", "128x4"};
@@ -320,7 +327,8 @@ constexpr int kNumDslashShapes64 = 4;
 static const char* kDslashShapes[] = {"128x4", "128x5", "128x6", "256x2", "128x4h", "128x5h", "128x6h", "256x2h"};
 constexpr int kNumDslashShapes = 8;
 
-void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st) {
+void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st,
+                   bool pdl) {
   const Geom& g = ctx->geom;
   if (prec == PREC_DF64) {
     QCD_REQUIRE(mode == MODE_D, QCD_ERR_ARG, "the double-float operator provides D only");
@@ -335,8 +343,8 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
   } else if (prec == QCD_PREC_DOUBLE) {
     QCD_REQUIRE(mode != MODE_A, QCD_ERR_ARG, "A is provided in float32 only");
     auto run = [&](int v) {
-      if (mode == MODE_D) launch_dslash_f64<MODE_D>(v, g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
-      else launch_dslash_f64<MODE_DDAG>(v, g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st);
+      if (mode == MODE_D) launch_dslash_f64<MODE_D>(v, g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st, pdl);
+      else launch_dslash_f64<MODE_DDAG>(v, g, out, in, ctx->u64, ctx->clov64, ctx->kappa, nrhs, st, pdl);
       check_launch();
     };
     char key[64];
@@ -348,9 +356,9 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
     const float k = (float)ctx->kappa;
     const void* clov = mode == MODE_A ? (const void*)ctx->cinv32 : (const void*)ctx->clov32;
     auto run = [&](int v) {
-      if (mode == MODE_A) launch_dslash_f32<MODE_A>(v, g, out, in, ctx->u32, clov, k, nrhs, st);
-      else if (mode == MODE_D) launch_dslash_f32<MODE_D>(v, g, out, in, ctx->u32, clov, k, nrhs, st);
-      else launch_dslash_f32<MODE_DDAG>(v, g, out, in, ctx->u32, clov, k, nrhs, st);
+      if (mode == MODE_A) launch_dslash_f32<MODE_A>(v, g, out, in, ctx->u32, clov, k, nrhs, st, pdl);
+      else if (mode == MODE_D) launch_dslash_f32<MODE_D>(v, g, out, in, ctx->u32, clov, k, nrhs, st, pdl);
+      else launch_dslash_f32<MODE_DDAG>(v, g, out, in, ctx->u32, clov, k, nrhs, st, pdl);
       check_launch();
     };
     char key[64];
@@ -628,7 +636,7 @@ extern "C" int qcd_apply_D(qcd_ctx* ctx, void* out, const void* in, int prec, in
   API_BEGIN
   require_operator(ctx);
   QCD_REQUIRE(out && in && out != in && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_apply_D: bad arguments");
-  dslash_launch(ctx, out, in, prec, dagger ? MODE_DDAG : MODE_D, nrhs, (cudaStream_t)stream);
+  dslash_launch(ctx, out, in, prec, dagger ? MODE_DDAG : MODE_D, nrhs, (cudaStream_t)stream, true);
   API_END(ctx)
 }
 
@@ -637,7 +645,7 @@ extern "C" int qcd_apply_A(qcd_ctx* ctx, void* out, const void* in, int nrhs, vo
   API_BEGIN
   require_operator(ctx);
   QCD_REQUIRE(out && in && out != in && nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_apply_A: bad arguments");
-  dslash_launch(ctx, out, in, QCD_PREC_SINGLE, MODE_A, nrhs, (cudaStream_t)stream);
+  dslash_launch(ctx, out, in, QCD_PREC_SINGLE, MODE_A, nrhs, (cudaStream_t)stream, true);
   API_END(ctx)
 }
 

@@ -34,6 +34,7 @@
 #include <cstdint>
 #include <functional>
 #include <string>
+#include <utility>
 
 #include "qcd_gb300.h"
 #include "df64.cuh"
@@ -595,6 +596,15 @@ __device__ __forceinline__ void clover_mul(const Ptr& cp, const Geom& g, int dom
 }
 
 // ---------------------------------------------------------------------------
+// programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor drains; it must call
+// pdl_wait() before touching anything the predecessor writes.  pdl_trigger()
+// lets the next such kernel start early.  Both are no-ops otherwise.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // context (host side)
 // ---------------------------------------------------------------------------
 struct Workspace;
@@ -694,7 +704,11 @@ int tune_pick(qcd_ctx* ctx, const char* key, int nvariants, const char* const* n
 void tuner_free(qcd_ctx* ctx);
 
 // internal entry points implemented in the other translation units
-void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st);
+// pdl: launch the float32/float64 operator with programmatic stream
+// serialization (back-to-back applications overlap their tails); off inside
+// the solver, where it measured slower
+void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st,
+                   bool pdl = false);
 void clover_apply_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int inverse, int nrhs,
                          cudaStream_t st);
 void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col, cudaStream_t st);
@@ -729,5 +743,22 @@ struct BatchDesc {
 };
 void dslash_batch_launch(const BatchDesc* d_desc, const int* d_block_lat, long long total_blocks, int dagger,
                          cudaStream_t st);
+
+// launch with programmatic stream serialization (see pdl_wait)
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  QCD_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 
 }  // namespace qcd

@@ -196,3 +196,22 @@ def test_fgmres_rejects_multi_rhs(c1):
     srcs = np.stack([point_source(c1.dims, 0, 0), point_source(c1.dims, 1, 1)])
     _, rc, _ = c1.lat.solve(srcs, nrhs=2, outer_restart=4, raise_on_error=False)
     assert rc == B.QCD_ERR_ARG
+
+
+@pytest.fixture(scope="module")
+def mixed_domains():
+    """8x8x4x8 with 2x4x2x4 domains and periodic t: the generic (any domain
+    shape) SAP kernel instead of the staged 4^4 one."""
+    p = Problem((8, 8, 4, 8), (2, 4, 2, 4), eps=0.3, kappa=0.12, csw=1.0, seed=1021, bc_t=1)
+    yield p
+    p.close()
+
+
+@pytest.mark.parametrize("sap_prec", ["single", "half", "half_gauge"])
+@pytest.mark.parametrize("use_graph", [0, 2])
+def test_solve_generic_domains(mixed_domains, sap_prec, use_graph):
+    b = gaussian_spinor(mixed_domains.dims, 2021)
+    x, rc, info = mixed_domains.lat.solve(b, tol=1e-10, inner_tol=1e-5, sap_prec=sap_prec, use_graph=use_graph)
+    x = to_np(x)
+    assert rc == 0 and info.true_resid < 1e-10
+    assert true_resid(mixed_domains.op, x, b) < 1e-10
