@@ -7,19 +7,22 @@
 // time (strides 1, 4, 16, 64).  At entry one thread arms an mbarrier and
 // issues two cp.async.bulk copies: the domain's links and its C_inv, each a
 // contiguous block of a staging layout built for this kernel.  While they
-// are in flight the threads read their s and evaluate the surface hops from
-// global memory; they then wait (bounded) on the barrier and run every
-// Jacobi sweep and the residual update from shared memory:
+// are in flight the threads read their s and evaluate the hops that leave
+// the domain (as face tasks, from global memory); they then wait (bounded)
+// on the barrier and run every Jacobi sweep and the residual update from
+// shared memory.  The launches of one M_SAP use programmatic dependent
+// launch: the staging copies are issued before the kernel waits for the
+// previous launch.
 //
 //   staging layouts per domain (global = shared):
-//     links  f16: __half2 [mu 4][site 256][9]     36 B per link, 32-bit reads
-//            f32: float2  [mu 4][site 256][9]     72 B per link, 64-bit reads
+//     links  f16: __half2 [mu 4][site 256][10]    40 B per link (9 + pad), 8-byte reads
+//            f32: float2  [mu 4][site 256][9]     72 B per link, 8-byte reads
 //     C_inv  f16: uint4   [site 256][11]          two blocks of 40 halves + pad
 //            f32: float4  [site 256][19]          two blocks of 36 floats + pad
-//   (the site strides 36/72 B and 176/304 B make each warp's reads free of
-//   shared-memory bank conflicts)
+//   (these site strides make each warp's reads free of shared-memory bank
+//   conflicts)
 //
-// Shared memory: f16 104 KB (two CTAs per SM), f32 172 KB (one CTA per SM).
+// Shared memory: f16 111 KB (two CTAs per SM), f32 176 KB (one CTA per SM).
 
 #include "qcd_internal.cuh"
 
