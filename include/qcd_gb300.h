@@ -179,7 +179,12 @@ int qcd_export_spinor(qcd_ctx* ctx, double* dst, const void* src, int prec, int 
 /* out = D in (dagger = 0) or D^dag in = gamma_5 D gamma_5 in (dagger = 1),
  * D x = (1 + C) x - kappa sum_mu [(1 - g_mu) U_mu(n) x(n+mu)
  *                                + (1 + g_mu) U_mu(n-mu)^dag x(n-mu)]   (App. A).
- * prec: QCD_PREC_DOUBLE or QCD_PREC_SINGLE.  out and in must not alias. */
+ * prec: QCD_PREC_DOUBLE or QCD_PREC_SINGLE.  out and in must not alias.
+ * The operator kernel is launched with programmatic stream serialization:
+ * it may start while the previous kernel on the stream drains and waits for
+ * that kernel's completion before it reads anything (back-to-back calls
+ * overlap their tails).  The first call for a given nrhs and precision
+ * times the compiled launch shapes (see qcd_set_tuning). */
 int qcd_apply_D(qcd_ctx* ctx, void* out, const void* in, int prec, int dagger, int nrhs,
                 void* stream);
 
@@ -237,8 +242,9 @@ int qcd_cdot(qcd_ctx* ctx, double result[2], const void* a, const void* b, int p
 
 /* Solve D x = b for nrhs right-hand sides (canonical float64 fields, host
  * memory when on_device = 0, device memory when 1).  Algorithm 4 in float64
- * around Algorithm 5 in float32 on (A M_SAP) y = C_inv r / |r|, the SAP
- * preconditioner in float32 or float16 storage.  With nrhs > 1 all right-hand
+ * (or flexible GMRES, see outer_restart) around Algorithm 5 in float32 on
+ * (A M_SAP) y = C_inv r / |r|, the SAP preconditioner in float32 or float16
+ * storage.  With nrhs > 1 all right-hand
  * sides advance together and share every gauge-field and clover load.
  * Returns QCD_OK when every rhs reached tol, QCD_ERR_NOT_CONVERGED,
  * QCD_ERR_BREAKDOWN or QCD_ERR_NONFINITE otherwise (x then holds the last
@@ -248,7 +254,7 @@ int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int on_device,
 
 /* Fill params with defaults: tol 1e-10, inner_tol 1e-6, max_outer 20,
  * max_inner 500, n_sap 4, n_jac 4, sap_prec SINGLE, use_graph 0,
- * residual_prec 1 (float64). */
+ * x_is_guess 0, residual_prec 1 (float64), outer_restart 0 (Algorithm 4). */
 int qcd_solve_params_default(qcd_solve_params* params);
 
 /* ---- ragged batches of lattices --------------------------------------- */
