@@ -65,3 +65,18 @@ def test_solve_params_layout_matches_header():
     ctypes_map = {"double": "c_double", "int": "c_int"}
     got = [(name, t.__name__) for name, t in binding.SolveParams._fields_]
     assert got == [(name, ctypes_map[t]) for t, name in fields]
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as C99 (no C++ or CUDA types in the ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "qcd_gb300.h"\n'
+                   'int main(void) { qcd_solve_params p; qcd_solve_params_default(&p); return p.n_sap == 4 ? 0 : 1; }\n')
+    res = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", os.path.dirname(HEADER), str(src)],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
