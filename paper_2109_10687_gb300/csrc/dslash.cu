@@ -513,7 +513,7 @@ __device__ __forceinline__ void df_clover_rows(const Geom& g, const DF64Spinor& 
       cx<df64> y = make_cx(df64(0.f), df64(0.f));
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        if (j == i) y = cmac(y, blk.diag(i), xv[j]);
+        if (j == i) y = make_cx(fma(blk.diagv(i), xv[j].re, y.re), fma(blk.diagv(i), xv[j].im, y.im));
         else if (j > i) y = cmac(y, blk.off(herm_off(i, j)), xv[j]);
         else y = cmacc(y, blk.off(herm_off(j, i)), xv[j]);
       }

@@ -306,7 +306,7 @@ __host__ __device__ __forceinline__ int herm_off(int i, int j) { return 5 * i - 
 template <typename R, typename Load>
 __device__ __forceinline__ void herm6_mul(Load blk, const cx<R> x[6], cx<R> y[6]) {
 #pragma unroll
-  for (int i = 0; i < 6; ++i) y[i] = blk.diag(i) * x[i];
+  for (int i = 0; i < 6; ++i) y[i] = blk.diagv(i) * x[i];  // real diagonal: 2 multiplies, not 4
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
@@ -516,12 +516,14 @@ struct CloverBlockF32 {
 };
 struct CloverBlockF64 {
   double r[36];
+  __device__ __forceinline__ double diagv(int i) const { return r[i]; }
   __device__ __forceinline__ cx<double> diag(int i) const { return make_cx(r[i], 0.0); }
   __device__ __forceinline__ cx<double> off(int k) const { return make_cx(r[6 + 2 * k], r[7 + 2 * k]); }
 };
 
 struct CloverBlockDF64 {
   df64 r[36];
+  __device__ __forceinline__ df64 diagv(int i) const { return r[i]; }
   __device__ __forceinline__ cx<df64> diag(int i) const { return make_cx(r[i], df64(0.f)); }
   __device__ __forceinline__ cx<df64> off(int k) const { return make_cx(r[6 + 2 * k], r[7 + 2 * k]); }
 };
