@@ -255,6 +255,31 @@ __device__ __forceinline__ void accumulate1(cx<R>& a0, cx<R>& a1, cx<R>& a2, cx<
   }
 }
 
+// acc = the projected spinor rebuilt from h (the first hop of a sum: no
+// additions to zero)
+template <int MU, int PM, typename R>
+__device__ __forceinline__ void rebuild(Spinor<R>& acc, const HalfSpinor<R>& h) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> h0 = h.h[0][c], h1 = h.h[1][c];
+    acc.v[0][c] = h0;
+    acc.v[1][c] = h1;
+    if (MU == 0) {
+      if (PM < 0) { acc.v[2][c] = times_mi(h1); acc.v[3][c] = times_mi(h0); }
+      else        { acc.v[2][c] = times_i(h1);  acc.v[3][c] = times_i(h0); }
+    } else if (MU == 1) {
+      if (PM < 0) { acc.v[2][c] = -h1; acc.v[3][c] = h0; }
+      else        { acc.v[2][c] = h1;  acc.v[3][c] = -h0; }
+    } else if (MU == 2) {
+      if (PM < 0) { acc.v[2][c] = times_mi(h0); acc.v[3][c] = times_i(h1); }
+      else        { acc.v[2][c] = times_i(h0);  acc.v[3][c] = times_mi(h1); }
+    } else {
+      if (PM < 0) { acc.v[2][c] = -h0; acc.v[3][c] = -h1; }
+      else        { acc.v[2][c] = h0;  acc.v[3][c] = h1; }
+    }
+  }
+}
+
 // acc += f * (projected spinor rebuilt from h); f = 1 unless a hop carries
 // the antiperiodic sign (a constant 1 folds to plain additions)
 template <int MU, int PM, typename R>

@@ -177,7 +177,9 @@ __device__ __forceinline__ void st_load_x(const float4* sx, int site, Spinor<flo
 // the domain reads the zero ghost site (and some valid link) and adds an
 // exact zero.  Straight-line code lets the compiler overlap the shared-memory
 // loads of several hops.  t: a warp has one t value, the branches are uniform.
-template <int MU, bool HALF>
+// FIRST: this direction's forward hop starts the sum (acc is assigned, not
+// added to); only for the branch-free directions
+template <int MU, bool HALF, bool FIRST = false>
 __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* sl, int s, Spinor<float>& acc) {
   constexpr int step = 1 << (2 * MU);
   const int c = lc<MU>(s);
@@ -189,7 +191,8 @@ __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* 
       project<MU, -1>(p, h);
       const SU3<float> u = StageT<HALF>::link(sl, MU, s);
       su3_mul(u, h, uh);
-      accumulate<MU, -1>(acc, uh);
+      if (FIRST) rebuild<MU, -1>(acc, uh);
+      else accumulate<MU, -1>(acc, uh);
     }
     {
       const int nb = c > 0 ? s - step : SX_GHOST + ((s - step) & 7);
@@ -407,11 +410,11 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
     Spinor<float> xk = src;
     const int napp = a.n_jac + (a.do_update ? 1 : 0);
     for (int it = 0; it < napp; ++it) {
-      zero(acc);
-      // t first: its warp-uniform branches then precede one straight-line
-      // stretch (x, y, z hops and the clover multiply) the compiler can schedule
+      // the x hops start the sum (no zeroing); the t hops' warp-uniform
+      // branches follow, then one straight-line stretch (y, z hops and the
+      // clover multiply)
+      st_intra<0, HALF, true>(sx, sl, s, acc);
       st_intra<3, HALF>(sx, sl, s, acc);
-      st_intra<0, HALF>(sx, sl, s, acc);
       st_intra<1, HALF>(sx, sl, s, acc);
       st_intra<2, HALF>(sx, sl, s, acc);
       st_clover<HALF>(sc, s, acc);
