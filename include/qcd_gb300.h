@@ -332,6 +332,24 @@ int qcd_tuning_report(qcd_ctx* ctx, char* buf, size_t len);
 /* Number of kernels the library has launched on this context so far. */
 int qcd_launch_count(const qcd_ctx* ctx, long long* count);
 
+/* ---- failure detection ------------------------------------------------- */
+
+/* Device status word: kernels record device-side failures here, e.g.
+ * QCD_ERR_TIMEOUT when the SAP block kernel's bounded wait for its staging
+ * copies gives up (the kernel then waits once more, also bounded, and
+ * returns; the context stays usable).  qcd_solve checks the word after every
+ * inner solve and returns its code.  *status = the word (QCD_OK if no failure);
+ * reset = 1 clears it.  Synchronises the stream. */
+int qcd_device_status(qcd_ctx* ctx, int* status, int reset, void* stream);
+
+/* Test hooks for the failure paths (the paper has no counterpart).  what:
+ * QCD_INJECT_NONE clears; QCD_INJECT_STAGING_WAIT makes the SAP block
+ * kernel's staging wait expect 16 bytes more than its copies bring, so the
+ * bounded wait runs out (about a second) and the kernel records
+ * QCD_ERR_TIMEOUT.  No GPU fault is involved. */
+enum { QCD_INJECT_NONE = 0, QCD_INJECT_STAGING_WAIT = 1 };
+int qcd_test_inject(qcd_ctx* ctx, int what);
+
 /* Measurement utility (no counterpart in the paper): the device's float32
  * FMA throughput in TFLOP/s (2 flop per FMA), from a kernel of independent
  * fused multiply-add chains over every SM, timed with CUDA events on

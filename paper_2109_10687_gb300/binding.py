@@ -90,6 +90,8 @@ _SIGS = {
                              ctypes.POINTER(SolveInfo), _P]),
     "qcd_tuning_report": (_I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "qcd_measure_fp32_peak": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P]),
+    "qcd_device_status": (_I, [_P, ctypes.POINTER(_I), _I, _P]),
+    "qcd_test_inject": (_I, [_P, _I]),
 }
 
 
@@ -289,6 +291,21 @@ def qcd_measure_fp32_peak(ctx, stream=None):
     v = ctypes.c_double()
     check(ctx, lib().qcd_measure_fp32_peak(ctx, ctypes.byref(v), _stream(stream)))
     return v.value
+
+
+INJECT_NONE = 0
+INJECT_STAGING_WAIT = 1
+
+
+def qcd_device_status(ctx, reset=False, stream=None):
+    """The device status word (QCD_OK, or e.g. QCD_ERR_TIMEOUT)."""
+    v = _I()
+    check(ctx, lib().qcd_device_status(ctx, ctypes.byref(v), int(bool(reset)), _stream(stream)))
+    return v.value
+
+
+def qcd_test_inject(ctx, what):
+    return check(ctx, lib().qcd_test_inject(ctx, int(what)))
 
 
 def qcd_tuning_report(ctx):

@@ -588,6 +588,24 @@ extern "C" int qcd_profile_read(qcd_ctx* ctx, int kc, long long* launches, doubl
   QCD_API_END(ctx)
 }
 
+extern "C" int qcd_device_status(qcd_ctx* ctx, int* status, int reset, void* stream) {
+  if (!ctx || !status) return QCD_ERR_ARG;
+  QCD_API_BEGIN(ctx)
+  cudaStream_t st = (cudaStream_t)stream;
+  int hs = 0;
+  QCD_CUDA_CHECK(cudaMemcpyAsync(&hs, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (reset) QCD_CUDA_CHECK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+  *status = hs;
+  QCD_API_END(ctx)
+}
+
+extern "C" int qcd_test_inject(qcd_ctx* ctx, int what) {
+  if (!ctx || what < QCD_INJECT_NONE || what > QCD_INJECT_STAGING_WAIT) return QCD_ERR_ARG;
+  ctx->inject = what;
+  return QCD_OK;
+}
+
 extern "C" int qcd_launch_count(const qcd_ctx* ctx, long long* count) {
   if (!ctx || !count) return QCD_ERR_ARG;
   *count = ctx->launches;

@@ -109,6 +109,7 @@ struct StagedArgs {
   const unsigned char* links;  // staging layout, all domains
   const unsigned char* clov;
   int* status;                 // word 0: set to QCD_ERR_TIMEOUT if a wait gives up
+  int extra_tx;                // testing: bytes the staging wait expects beyond its copies
 };
 
 // ---------------------------------------------------------------------------
@@ -141,11 +142,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: about 2^22 polls (each try_wait itself suspends for a while);
-// returns false when it gives up.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up (returns false) after half a second of polling, or
+// 2^24 polls, whichever comes first.  The copies it waits for take
+// microseconds.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (int i = 0; i < (1 << 22); ++i)
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < (1 << 24); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > 500000000ull) return false;
+  }
   return false;
 }
 
@@ -363,7 +373,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (s == 0) {
     mbar_init(bar, 1);
-    mbar_expect_tx(bar, ST::LINK_BYTES + ST::CLOV_BYTES);
+    mbar_expect_tx(bar, ST::LINK_BYTES + ST::CLOV_BYTES + a.extra_tx);
     bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, bar);
     bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, bar);
   }
@@ -538,6 +548,9 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
   a.links = (const unsigned char*)(HALF ? ctx->st_link16 : ctx->st_link32);
   a.clov = (const unsigned char*)(HALF ? ctx->st_clov16 : ctx->st_clov32);
   a.status = ctx->d_status;
+  // test hook: wait for 16 bytes that no copy brings, so that the bounded
+  // wait gives up and reports QCD_ERR_TIMEOUT
+  a.extra_tx = ctx->inject == QCD_INJECT_STAGING_WAIT ? 16 : 0;
   const int smem = SX_BYTES + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 16;
   for (int sweep = 0; sweep <= n_sap; ++sweep) {
     a.s_in32 = sweep == 0 ? s_first_in32 : F32Spinor{nullptr};

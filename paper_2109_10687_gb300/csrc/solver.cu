@@ -1046,6 +1046,9 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   } else {
     QCD_CUDA_CHECK(cudaMemsetAsync(w->x64, 0, n2 * sizeof(double2) * nrhs, st));
   }
+  // device-side failures (a bounded wait that gave up) are read with every residual
+  int dev_status = QCD_OK;
+  QCD_CUDA_CHECK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   auto residual = [&]() {
     if (df) {
       dslash_launch(ctx, rdf, xdf, PREC_DF64, MODE_D, nrhs, st);
@@ -1059,6 +1062,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
       check_launch();
     }
     QCD_CUDA_CHECK(cudaMemcpyAsync(h_r2.data(), d_red + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    QCD_CUDA_CHECK(cudaMemcpyAsync(&dev_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaStreamSynchronize(st));
   };
   if (P.x_is_guess) {
@@ -1106,6 +1110,10 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double), cudaMemcpyHostToDevice, st));
     bool stop = false;
     while (!stop) {
+      if (dev_status == QCD_ERR_TIMEOUT) {
+        result = QCD_ERR_TIMEOUT;
+        break;
+      }
       worst_rel = rel(0);
       if (!std::isfinite(h_r2[0])) {
         result = QCD_ERR_NONFINITE;
@@ -1141,6 +1149,13 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
         inner_total += bicgstab_sap(ctx, w, w->tmp32, 1, P, st, &st_inner);
         last_inner_status = st_inner;
         if (st_inner == QCD_ERR_BREAKDOWN) ++breakdowns;
+        QCD_CUDA_CHECK(cudaMemcpyAsync(&dev_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+        if (dev_status == QCD_ERR_TIMEOUT) {
+          result = QCD_ERR_TIMEOUT;
+          stop = true;
+          break;
+        }
         if (st_inner == QCD_ERR_NONFINITE) {
           result = QCD_ERR_NONFINITE;
           stop = true;
@@ -1214,6 +1229,10 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     }
   } else {
   for (;;) {
+    if (dev_status == QCD_ERR_TIMEOUT) {
+      result = QCD_ERR_TIMEOUT;
+      break;
+    }
     worst_rel = 0.0;
     bool finite = true;
     for (int r = 0; r < nrhs; ++r) {
@@ -1244,6 +1263,12 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     inner_total += bicgstab_sap(ctx, w, w->tmp32, nrhs, P, st, &st_inner);
     last_inner_status = st_inner;
     if (st_inner == QCD_ERR_BREAKDOWN) ++breakdowns;
+    QCD_CUDA_CHECK(cudaMemcpyAsync(&dev_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QCD_CUDA_CHECK(cudaStreamSynchronize(st));
+    if (dev_status == QCD_ERR_TIMEOUT) {
+      result = QCD_ERR_TIMEOUT;
+      break;
+    }
     if (st_inner == QCD_ERR_NONFINITE) {
       result = QCD_ERR_NONFINITE;
       break;
@@ -1280,6 +1305,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   if (result != QCD_OK) {
     ctx->err = result == QCD_ERR_NOT_CONVERGED ? "qcd_solve: tolerance not reached"
                : result == QCD_ERR_BREAKDOWN   ? "qcd_solve: BiCGStab breakdown"
+               : result == QCD_ERR_TIMEOUT     ? "qcd_solve: a bounded device-side wait gave up"
                                                : "qcd_solve: non-finite residual";
     return result;
   }

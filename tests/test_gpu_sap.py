@@ -63,3 +63,28 @@ def test_sap_reduces_residual(prob):
     b = prob.source(2104)
     amb = to_np(prob.lat.sap(b, 4, 4, "single", with_A=True))
     assert rel_l2(amb, b) < 0.5
+
+
+def test_staging_wait_timeout_is_reported_and_context_survives():
+    """Failure path of the SAP block kernel's bounded wait, without a GPU fault:
+    the test hook makes the wait expect 16 bytes that no copy brings, so it
+    runs out (half a second), the kernel records QCD_ERR_TIMEOUT, waits once
+    more (bounded) and returns.  The status reaches the host, a solve reports
+    it, and with the hook cleared the same context computes M_SAP correctly."""
+    from paper_2109_10687_gb300 import binding as B
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), eps=0.3, kappa=0.12, csw=1.0, seed=1101)
+    try:
+        b = p.source(2106)
+        B.qcd_test_inject(p.lat.ctx, B.INJECT_STAGING_WAIT)
+        p.lat.sap(b, 0, 1, "half")
+        assert B.qcd_device_status(p.lat.ctx, reset=True) == B.QCD_ERR_TIMEOUT
+        _, rc, _ = p.lat.solve(b, tol=1e-10, n_sap=0, n_jac=1, max_inner=1, max_outer=1, sap_prec="half",
+                               raise_on_error=False)
+        assert rc == B.QCD_ERR_TIMEOUT
+        B.qcd_test_inject(p.lat.ctx, B.INJECT_NONE)
+        B.qcd_device_status(p.lat.ctx, reset=True)
+        got = to_np(p.lat.sap(b, 4, 4, "half"))
+        assert B.qcd_device_status(p.lat.ctx) == B.QCD_OK
+        assert rel_l2(got, sap.msap(p.op, b, 4, 4)) <= 5e-3
+    finally:
+        p.close()
