@@ -86,9 +86,10 @@ __device__ __forceinline__ void hop_dir(const Geom& g, const SIO& in, const LP& 
 // all eight hops are independent straight-line code the compiler can issue
 // early (the operator is bound by how many loads are in flight).  nb holds
 // the eight neighbour domains of dom, tf its boundary-sign flags.
-template <int MU, int PMF, int PMB, typename R, typename SIO, typename LP>
+template <int MU, int PMF, int PMB, bool FIRST, typename R, typename SIO, typename LP>
 __device__ __forceinline__ void hop_dir_bf(const Geom& g, const SIO& in, const LP& U, int dom, int s, int rhs_off,
                                            const int nb[8], int tf, Spinor<R>& acc) {
+  static_assert(!FIRST || MU < 3, "the first hop must carry no boundary sign");
   const int c = (s >> g.shift[MU]) & (g.d[MU] - 1);
   const int step = 1 << g.shift[MU];
   const int span = (g.d[MU] - 1) * step;
@@ -104,7 +105,8 @@ __device__ __forceinline__ void hop_dir_bf(const Geom& g, const SIO& in, const L
     SU3<R> u;
     U.load(g, dom, MU, s, u);
     su3_mul(u, h, uh);
-    accumulate<MU, PMF>(acc, uh, f);
+    if (FIRST) rebuild<MU, PMF>(acc, uh);  // f = 1: the sign is for t hops only
+    else accumulate<MU, PMF>(acc, uh, f);
   }
   {
     const bool inside = c > 0;
@@ -131,11 +133,10 @@ __device__ __forceinline__ void hopping_bf(const Geom& g, const SIO& in, const L
   nb[0] = n0.x; nb[1] = n0.y; nb[2] = n0.z; nb[3] = n0.w;
   nb[4] = n1.x; nb[5] = n1.y; nb[6] = n1.z; nb[7] = n1.w;
   const int tf = __ldg(g.tflag + dom);
-  zero(acc);
-  hop_dir_bf<0, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
-  hop_dir_bf<1, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
-  hop_dir_bf<2, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
-  hop_dir_bf<3, PMF, PMB>(g, in, U, dom, s, rhs_off, nb, tf, acc);
+  hop_dir_bf<0, PMF, PMB, true>(g, in, U, dom, s, rhs_off, nb, tf, acc);  // starts the sum
+  hop_dir_bf<1, PMF, PMB, false>(g, in, U, dom, s, rhs_off, nb, tf, acc);
+  hop_dir_bf<2, PMF, PMB, false>(g, in, U, dom, s, rhs_off, nb, tf, acc);
+  hop_dir_bf<3, PMF, PMB, false>(g, in, U, dom, s, rhs_off, nb, tf, acc);
 }
 
 template <int PMF, int PMB, int FILTER, typename R, typename SIO, typename LP>
