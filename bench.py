@@ -274,7 +274,7 @@ def main():
                     help="profiling case: set up the workload and run only REPS applications of one kernel")
     ap.add_argument("--lattice", type=int, default=32, help="lattice extent of the profiling case")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5ragged"],
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5ragged", "n2"],
                     help="c2 (default) is the benchmark line; the others measure the other workloads")
     args = ap.parse_args()
     if args.config != "c2":

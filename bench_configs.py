@@ -226,9 +226,59 @@ def c5ragged(args):
                         "inner_max": max(i.inner_iters for i in infos)}}
 
 
+# Per-site flop of one SAP-BiCGStab iteration in the paper's accounting
+# (Sec. 4; reproduces its Tables 2-3): 168 flop per hop (156 for a temporal
+# hop in the paper's basis, 168 in the chiral basis used here), 600 per C_inv
+# apply with the axpy, 48 per residual update.
+def _paper_flop_per_site_iter(domain, n_sap, n_jac, hops=(168, 168, 168, 168)):
+    f_in = 600 + sum(2 * (1 - 1 / d) * h for d, h in zip(domain, hops))
+    inner = vol = 1
+    for d in domain:
+        inner *= max(d - 2, 0)
+        vol *= d
+    f_out = sum(2 / d * h for d, h in zip(domain, hops)) + 600 * (1 - inner / vol)
+    return 2 * (n_sap + 1) * (f_in + n_jac * (f_in + 48) + f_out) + 96 * n_sap + 48 + 1008
+
+
+def n2(args):
+    """The paper's algorithm parameters (n_sap 4, n_jac 2, float32 SAP-BiCGStab)
+    on 32^4 with this build's 4^4 domains (the paper's 16x6x4x3 domains are
+    not power-of-two shapes): BiCGStab iterations per second from the
+    difference of two fixed-length solves, and the rate in the paper's flop
+    accounting.  Paper, one A64FX node (4 processes): 1.38e7 site-iterations/s,
+    0.83 TFLOPS (Table 2, first row)."""
+    from lattice_inputs import gaussian_spinor
+    from paper_2109_10687_gb300 import binding as B
+    dims, domain, n_sap, n_jac = (32, 32, 32, 32), (4, 4, 4, 4), 4, 2
+    lat = _lat(dims, 0.3, 0.125, 1.0, 1001)
+    b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2001))).cuda().contiguous()
+    x = torch.zeros_like(b)
+    vol = int(np.prod(dims))
+    flop = _paper_flop_per_site_iter(domain, n_sap, n_jac)
+    out = {"flop_per_site_iteration": flop}
+    for name, prec in (("float32", "single"), ("float16_storage", "half")):
+        times = {}
+        for iters in (10, 30):
+            p = _params(prec, 1e-30, 2)
+            p.n_sap, p.n_jac = n_sap, n_jac
+            p.inner_tol, p.max_inner, p.max_outer = 1e-30, iters, 1
+            B.qcd_solve(lat.ctx, x, b, 1, p, raise_on_error=False)
+            t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, p, raise_on_error=False), 3)
+            times[iters] = (t, info.inner_iters)
+        (t1, i1), (t2, i2) = times[10], times[30]
+        t_iter = (t2 - t1) / max(1, i2 - i1)
+        out[name] = {"ms_per_iteration": 1e3 * t_iter, "iterations": [i1, i2],
+                     "site_iterations_per_s": vol / t_iter, "tflops_paper_accounting": flop * vol / t_iter / 1e12,
+                     "vs_a64fx_node_site_iterations": vol / t_iter / 1.38e7}
+    return {"config": {"workload": "32^4, eps 0.3, kappa 0.125, c_sw 1.0; SAP-BiCGStab with the paper's n_sap 4, "
+                                   "n_jac 2 on 4^4 domains; fixed iteration counts (graph loop)"},
+            "metric": "BiCGStab iterations: site-iterations/s and TFLOPS in the paper's flop accounting",
+            "unit": "site-iterations/s", "results": out}
+
+
 def run(args):
     torch.cuda.set_device(0)
-    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "c5ragged": c5ragged}[args.config]
+    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "c5ragged": c5ragged, "n2": n2}[args.config]
     line = fn(args)
     line["name"] = args.config
     print(json.dumps(line))
