@@ -86,3 +86,40 @@ def test_zero_rhs_rejected():
         assert rc == B.QCD_ERR_ARG
     finally:
         lat.close()
+
+
+def test_solve_64x4_sampled():
+    """The 64^4 workload (eps 0.2, kappa 0.126, c_SW 1.1) at full size: the
+    float32 D on 24 sampled sites and the mixed-precision solve's residual on
+    48 sampled sites, both recomputed by the site-by-site float64 oracle."""
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300.lattice import Lattice
+    dims = (64, 64, 64, 64)
+    kappa, csw = 0.126, 1.1
+    u = random_su3_field_fast(dims, 0.2, 1501)
+    lat = Lattice(dims, (4, 4, 4, 4), -1, "chiral").setup(u, kappa, csw)
+    try:
+        g = gamma_chiral()
+        b = gaussian_spinor(dims, 2501)
+        rng = np.random.default_rng(13)
+        d32 = to_np(lat.apply_D(b, "single"))
+        num = den = 0.0
+        for _ in range(24):
+            c = tuple(int(rng.integers(0, 64)) for _ in range(4))
+            ref = pointwise.D_at(u, b, c, kappa, csw, g, -1)
+            num += np.sum(np.abs(d32[c[3], c[2], c[1], c[0]] - ref) ** 2)
+            den += np.sum(np.abs(ref) ** 2)
+        assert np.sqrt(num / den) <= 1e-6
+        del d32
+        x, rc, info = lat.solve(b, tol=1e-10, inner_tol=1e-5, sap_prec="half", use_graph=2, max_inner=2000)
+        assert rc == 0 and info.true_resid < 1e-10
+        x = to_np(x)
+        num = den = 0.0
+        for _ in range(48):
+            c = tuple(int(rng.integers(0, 64)) for _ in range(4))
+            r = b[c[3], c[2], c[1], c[0]] - pointwise.D_at(u, x, c, kappa, csw, g, -1)
+            num += np.sum(np.abs(r) ** 2)
+            den += np.sum(np.abs(b[c[3], c[2], c[1], c[0]]) ** 2)
+        assert np.sqrt(num / den) < 1e-8
+    finally:
+        lat.close()
