@@ -45,8 +45,20 @@ def _compile(nvcc, src, obj, extra):
 
 
 def build(verbose=False, ptxas_info=False, force=False):
-    """Compile every kernel source and link the shared library; returns its path."""
+    """Compile every kernel source and link the shared library; returns its path.
+    Concurrent callers (several ranks on one node) serialise on a lock file, so
+    only the first compiles and the others find the library up to date."""
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, ptxas_info, force)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, ptxas_info, force):
     nvcc = nvcc_path()
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
