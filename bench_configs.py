@@ -124,12 +124,12 @@ def c3(args):
     # 12 sequential plain float32 solves of the same sources
     b1 = [b[i].contiguous() for i in range(12)]
     x1 = torch.zeros_like(b1[0])
-    B.qcd_solve(lat.ctx, x1, b1[0], 1, _params("single", graph=0))
+    B.qcd_solve(lat.ctx, x1, b1[0], 1, _params("single", graph=2))
     t0 = time.perf_counter()
     worst = 0.0
     iters = 0
     for i in range(12):
-        rc, info = B.qcd_solve(lat.ctx, x1, b1[i], 1, _params("single", graph=0))
+        rc, info = B.qcd_solve(lat.ctx, x1, b1[i], 1, _params("single", graph=2))
         worst = max(worst, info.true_resid)
         iters += info.inner_iters
     torch.cuda.synchronize()
@@ -141,7 +141,7 @@ def c3(args):
     return {"config": {"workload": "48^4, eps 0.25, kappa 0.125, c_sw 1.1, 12 spin-colour point sources at the "
                                    "origin; batched float16-storage SAP + float32 BiCGStab + float64 "
                                    "correction to 1e-10 (device-side graph loop) vs 12 sequential plain float32 "
-                                   "solves"},
+                                   "solves (also with the graph loop)"},
             "metric": "time to FP64 residual 1e-10 for 12 right-hand sides", "unit": "s", "results": out}
 
 
