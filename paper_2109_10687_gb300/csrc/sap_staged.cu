@@ -238,9 +238,10 @@ __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* 
 
 // Surface term as face tasks.  The hops that leave a 4^4 domain start on its
 // eight faces (direction MU, side 0: sites with c_MU = 3, forward hop; side 1:
-// c_MU = 0, backward hop), 64 sites each, 512 per domain.  Thread tau takes
-// task tau (directions 0, 1) and task tau + 256 (directions 2, 3); a warp's
-// 32 tasks share direction and side, so no lane idles (with one thread per
+// c_MU = 0, backward hop), 64 sites each, 512 per domain.  Warps 0-3 take
+// the x and z faces and warps 4-7 the y and t faces, one task of each
+// direction per thread; a warp's 32 tasks share direction and side (warps
+// 2 w and 2 w + 1 cover one side's 64 sites), so no lane idles (with one thread per
 // site, each face hop is a branch that a quarter of the lanes take).  The
 // hop result U P x (a half spinor) goes to a slot in shared memory; the
 // site's thread adds the slots of its faces afterwards.
