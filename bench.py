@@ -44,22 +44,28 @@ D_FLOP_PER_SITE = 1824
 
 def sap_bytes_per_site(prec):
     """Algorithmic bytes per site of one SAP half-sweep launch, averaged over
-    the launches of one M_SAP (n_sap + 1 sweeps, two colours):
-    read s, b, own links, C_inv, the neighbouring domains' x across the
-    surface (2 sites per site for 4^4 domains) and the crossing backward links
-    (1 per site); write x and s."""
+    the launches of one M_SAP (n_sap + 1 sweeps, two colours): read s (the
+    float32 source in the first sweep), the domain's links and C_inv, and
+    with a surface term the domain's halo (one float32 half spinor per hop
+    that enters the domain: 2 per site for 4^4 domains, 96 B); write the halo
+    of the other colour's domains (96 B, all but the last launch); then
+    either the residual update (read b in float32, write s) or, in the last
+    sweep, the float32 result x."""
     sp = 96 if prec == "single" else 52
     link = 72 if prec == "single" else 36
     clov = 288 if prec == "single" else 144
-    base = sp + 4 * link + clov + sp                    # s in, links, C_inv, x out
-    surf = 2 * sp + link                                # halo spinors + crossing links
-    upd = 96 + sp                                       # b (float32) in, s out
+    halo = 96
     seq = []
     for sweep in range(N_SAP + 1):
         last = sweep == N_SAP
         for colour in (0, 1):
-            has_surf = not (sweep == 0 and colour == 0)
-            seq.append(base + (surf if has_surf else 0) + (0 if last else upd))
+            nb = (96 if sweep == 0 else sp) + 4 * link + clov
+            if not (sweep == 0 and colour == 0):
+                nb += halo                       # halo in
+            if not (last and colour == 1):
+                nb += halo                       # halo out
+            nb += 96 if last else 96 + sp        # x out, or b in and s out
+            seq.append(nb)
     return sum(seq) / len(seq)
 
 

@@ -743,12 +743,15 @@ void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col
 void build_clover_launch(qcd_ctx* ctx, cudaStream_t st);
 void build_sap_staging(qcd_ctx* ctx, cudaStream_t st);
 bool sap_staged_available(const qcd_ctx* ctx);
-void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
-                             int n_sap, int n_jac, cudaStream_t st);
-void sap_staged_sequence_f16(qcd_ctx* ctx, F32Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b,
-                             F32Spinor x_out, int nrhs, int n_sap, int n_jac, cudaStream_t st);
-void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
-                              int n_sap, int n_jac, cudaStream_t st);
+// halo: face halo of the shared-memory SAP kernel, 96 bytes per site and right-hand side
+void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b,
+                             float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st);
+void sap_staged_sequence_f16(qcd_ctx* ctx, F32Spinor s_first_in, F16Spinor s, F32Spinor b, F32Spinor x_out,
+                             float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st);
+void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b,
+                              float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st);
+// ws_x16 holds 96 bytes per site and right-hand side: the float16 x of the
+// generic kernel, or the face halo of the shared-memory kernel
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                       void* ws_s, void* ws_x16, void* ws_b16, cudaStream_t st);
 void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);

@@ -263,8 +263,9 @@ static void sap_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spinor b
 }
 
 // x = M_SAP b for nrhs stacked float32 fields.  ws_s holds s (float32 or
-// float16), ws_x16 / ws_b16 the float16 x and source (sap_prec == HALF); all
-// three are sized for nrhs right-hand sides.  With the shared-memory kernel
+// float16), ws_x16 / ws_b16 the float16 x and source of the generic kernel
+// (sap_prec == HALF); ws_x16 is also the shared-memory kernel's face halo
+// (96 bytes per site).  All three are sized for nrhs right-hand sides.  With the shared-memory kernel
 // all right-hand sides go through each launch and share its staged links and
 // C_inv; the generic kernel runs them one after the other.
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
@@ -277,7 +278,7 @@ void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_
     // float16 links and C_inv, float32 vectors
     if (staged) {
       F32Spinor xs{x}, bs{(float4*)b}, ss{(float4*)ws_s};
-      sap_staged_sequence_h16g(ctx, bs, ss, xs, bs, nrhs, n_sap, n_jac, st);
+      sap_staged_sequence_h16g(ctx, bs, ss, xs, bs, (float4*)ws_x16, nrhs, n_sap, n_jac, st);
     } else {
       for (int r = 0; r < nrhs; ++r) {
         F32Spinor xs{x + r * v4}, bs{(float4*)b + r * v4}, ss{(float4*)ws_s + r * v4};
@@ -290,7 +291,7 @@ void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_
   if (sap_prec == QCD_PREC_SINGLE) {
     if (staged) {
       F32Spinor xs{x}, bs{(float4*)b}, ss{(float4*)ws_s};
-      sap_staged_sequence_f32(ctx, bs, ss, xs, bs, nrhs, n_sap, n_jac, st);
+      sap_staged_sequence_f32(ctx, bs, ss, xs, bs, (float4*)ws_x16, nrhs, n_sap, n_jac, st);
     } else {
       for (int r = 0; r < nrhs; ++r) {
         F32Spinor xs{x + r * v4}, bs{(float4*)b + r * v4}, ss{(float4*)ws_s + r * v4};
@@ -308,8 +309,8 @@ void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_
   if (staged) {
     // the first sweep reads the float32 source and the last one writes the
     // float32 result: no conversion launches
-    sap_staged_sequence_f16(ctx, F32Spinor{(float4*)b}, s16, x16, F32Spinor{(float4*)b}, F32Spinor{x}, nrhs, n_sap,
-                            n_jac, st);
+    sap_staged_sequence_f16(ctx, F32Spinor{(float4*)b}, s16, F32Spinor{(float4*)b}, F32Spinor{x}, (float4*)ws_x16,
+                            nrhs, n_sap, n_jac, st);
     return;
   }
   {

@@ -7,12 +7,21 @@
 // time (strides 1, 4, 16, 64).  At entry one thread arms an mbarrier and
 // issues two cp.async.bulk copies: the domain's links and its C_inv, each a
 // contiguous block of a staging layout built for this kernel.  While they
-// are in flight the threads read their s and evaluate the hops that leave
-// the domain (as face tasks, from global memory); they then wait (bounded)
-// on the barrier and run every Jacobi sweep and the residual update from
-// shared memory.  The launches of one M_SAP use programmatic dependent
-// launch: the staging copies are issued before the kernel waits for the
-// previous launch.
+// are in flight the threads read their s and the domain's halo; they then
+// wait (bounded) on the barrier and run every Jacobi sweep and the residual
+// update from shared memory.  The launches of one M_SAP use programmatic
+// dependent launch: the staging copies are issued before the kernel waits
+// for the previous launch.
+//
+// Halo.  The surface term of a colour-c launch needs, for each hop that
+// enters the domain, U P x of the neighbouring (other-colour) domain's
+// iterate.  The launch that computed that iterate still holds it, and its
+// own links, in shared memory, so it finishes the work there: for each of
+// its face sites it writes the half spinor the neighbour needs into the
+// neighbour's halo slots, U^dag P+ x for a backward hop (complete) and P- x
+// for a forward hop (the receiver multiplies by its own link U, which it has
+// staged).  The receiving launch reads its halo with coalesced loads and no
+// neighbour lookups.  This is the exchange of Sec. 4.1, done through memory.
 //
 //   staging layouts per domain (global = shared):
 //     links  f16: __half2 [mu 4][site 256][10]    40 B per link (9 + pad), 8-byte reads
@@ -23,6 +32,8 @@
 //   conflicts)
 //
 // Shared memory: f16 111 KB (two CTAs per SM), f32 176 KB (one CTA per SM).
+// Two mbarriers: the staging copies (once) and the halo copy (once per
+// right-hand side, parity r & 1).
 
 #include "qcd_internal.cuh"
 
@@ -105,7 +116,9 @@ struct StagedArgs {
   F32Spinor b;
   F32Spinor s_in32;      // if set: the sweep's input is read from this float32 field instead of s_in
   F32Spinor x_out32;     // if set: the iterate is also stored to this float32 field
-  int x_store;           // store the iterate in x (0 when no later launch reads it)
+  int x_store;           // store the iterate in x (the result of M_SAP)
+  int do_halo;           // write the neighbours' halo (0 in the last launch)
+  float4* halo;          // [rhs][domain][face 8][3][64] float4, face = 2 MU + side
   const unsigned char* links;  // staging layout, all domains
   const unsigned char* clov;
   int* status;                 // word 0: set to QCD_ERR_TIMEOUT if a wait gives up
@@ -236,17 +249,17 @@ __device__ __forceinline__ void st_intra(const float4* sx, const unsigned char* 
   }
 }
 
-// Surface term as face tasks.  The hops that leave a 4^4 domain start on its
-// eight faces (direction MU, side 0: sites with c_MU = 3, forward hop; side 1:
-// c_MU = 0, backward hop), 64 sites each, 512 per domain.  Warps 0-3 take
-// the x and z faces and warps 4-7 the y and t faces, one task of each
-// direction per thread; a warp's 32 tasks share direction and side (warps
-// 2 w and 2 w + 1 cover one side's 64 sites), so no lane idles (with one thread per
-// site, each face hop is a branch that a quarter of the lanes take).  The
-// hop result U P x (a half spinor) goes to a slot in shared memory; the
-// site's thread adds the slots of its faces afterwards.
+// Surface term as face tasks.  The hops that enter a 4^4 domain from its
+// neighbours end on its eight faces (direction MU, side 0: sites with
+// c_MU = 3, forward hop; side 1: c_MU = 0, backward hop), 64 sites each, 512
+// per domain.  Thread tau takes face site f = tau & 63 of both sides of
+// direction MU = tau >> 6 (two warps per direction, so the branches on MU
+// are warp-uniform and no lane idles).  A task's result U P x (a half
+// spinor) goes to a slot in shared memory; the site's thread adds the slots
+// of its faces afterwards.
 // Slots: float4 [MU 4][side 2][3][64] = 24 KB at the start of the x buffer (not
 // yet in use; the ghost sites it overlaps are cleared before x is stored).
+// The halo has the slots' layout, one block per domain and right-hand side.
 __device__ __forceinline__ int face_site(int mu, int side, int f) {
   const int lo = f & ((1 << (2 * mu)) - 1);
   const int hi = f >> (2 * mu);
@@ -260,36 +273,105 @@ __device__ __forceinline__ int face_index(int mu, int s) {
 __device__ __forceinline__ float4* face_slot(float4* slots, int mu, int side, int k, int f) {
   return slots + ((mu * 2 + side) * 3 + k) * 64 + f;
 }
-
-template <int MU, bool HALF, typename SIO>
-__device__ __forceinline__ void st_face_task(const Geom& g, const SIO& x, const unsigned char* links, int dom,
-                                             int rhs_off, int side, int f, float4* slots) {
-  constexpr int step = 1 << (2 * MU);
-  constexpr size_t dom_bytes = StageT<HALF>::LINK_BYTES;
-  const int s = face_site(MU, side, f);
-  const int nd = __ldg(g.nbr + dom * 8 + 2 * MU + side);
-  const int sign = ((__ldg(g.tflag + dom) >> (2 * MU + side)) & 1) ? g.bc_t : 1;
-  Spinor<float> p;
-  HalfSpinor<float> h, uh;
-  if (side == 0) {
-    x.load(g, nd + rhs_off, s - 3 * step, p);
-    project<MU, -1>(p, h);
-    const SU3<float> u = StageT<HALF>::link(links + dom * dom_bytes, MU, s);
-    su3_mul(u, h, uh);
-  } else {
-    const int ns = s + 3 * step;
-    x.load(g, nd + rhs_off, ns, p);
-    project<MU, +1>(p, h);
-    const SU3<float> u = StageT<HALF>::link(links + nd * dom_bytes, MU, ns);
-    su3_dag_mul(u, h, uh);
-  }
-  if (sign < 0) scale_half(uh, -1.0f);
+__device__ __forceinline__ float4* halo_slot(float4* halo, int domr, int mu, int side, int k, int f) {
+  return halo + ((size_t)(domr * 8 + mu * 2 + side) * 3 + k) * 64 + f;
+}
+__device__ __forceinline__ void half_to_f4(const HalfSpinor<float>& h, float4 v[3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const cx<float> a0 = uh.h[(2 * k) / 3][(2 * k) % 3];
-    const cx<float> a1 = uh.h[(2 * k + 1) / 3][(2 * k + 1) % 3];
-    *face_slot(slots, MU, side, k, f) = make_float4(a0.re, a0.im, a1.re, a1.im);
+    const cx<float> a0 = h.h[(2 * k) / 3][(2 * k) % 3];
+    const cx<float> a1 = h.h[(2 * k + 1) / 3][(2 * k + 1) % 3];
+    v[k] = make_float4(a0.re, a0.im, a1.re, a1.im);
   }
+}
+__device__ __forceinline__ void f4_to_half(const float4 v[3], HalfSpinor<float>& h) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    h.h[(2 * k) / 3][(2 * k) % 3] = make_cx(v[k].x, v[k].y);
+    h.h[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v[k].z, v[k].w);
+  }
+}
+
+// Producer: after the sweeps, x (in shared memory) is this domain's final
+// iterate.  Thread tau handles face site f of both sides of direction MU:
+// the side-0 site (c_MU = 3) sends U_MU(m)^dag P+ x(m) to the forward
+// neighbour, whose backward hop it is; the side-1 site (c_MU = 0) sends
+// P- x(m) to the backward neighbour, whose forward hop it is.  The face index
+// f is the same on both ends of a hop.
+template <int MU, bool HALF>
+__device__ __forceinline__ void st_halo_out_dir(const Geom& g, const float4* sx, const unsigned char* sl,
+                                                float4* halo, int dom, int rhs_off, int f) {
+  {
+    const int m = face_site(MU, 0, f);
+    Spinor<float> p;
+    st_load_x(sx, m, p);
+    HalfSpinor<float> h, uh;
+    project<MU, +1>(p, h);
+    const SU3<float> u = StageT<HALF>::link(sl, MU, m);
+    su3_dag_mul(u, h, uh);
+    float4 v[3];
+    half_to_f4(uh, v);
+    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU) + rhs_off;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) *halo_slot(halo, nd, MU, 1, k, f) = v[k];
+  }
+  {
+    const int m = face_site(MU, 1, f);
+    Spinor<float> p;
+    st_load_x(sx, m, p);
+    HalfSpinor<float> h;
+    project<MU, -1>(p, h);
+    float4 v[3];
+    half_to_f4(h, v);
+    const int nd = __ldg(g.nbr + dom * 8 + 2 * MU + 1) + rhs_off;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) *halo_slot(halo, nd, MU, 0, k, f) = v[k];
+  }
+}
+template <bool HALF>
+__device__ __forceinline__ void st_halo_out(const Geom& g, const float4* sx, const unsigned char* sl, float4* halo,
+                                            int dom, int rhs_off, int s) {
+  const int f = s & 63;
+  switch (s >> 6) {  // warp-uniform
+    case 0: st_halo_out_dir<0, HALF>(g, sx, sl, halo, dom, rhs_off, f); break;
+    case 1: st_halo_out_dir<1, HALF>(g, sx, sl, halo, dom, rhs_off, f); break;
+    case 2: st_halo_out_dir<2, HALF>(g, sx, sl, halo, dom, rhs_off, f); break;
+    default: st_halo_out_dir<3, HALF>(g, sx, sl, halo, dom, rhs_off, f); break;
+  }
+}
+
+// Receiver: the domain's halo block has the layout of the slots and arrives
+// there by one bulk copy.  Then, with the links staged, the forward hop's
+// P- x is multiplied in place by this domain's U_MU(n); the backward hop's
+// U^dag P+ x is complete.  Only t faces can carry the antiperiodic sign.
+constexpr int HALO_F4 = 8 * 3 * 64;              // float4 per domain
+constexpr unsigned HALO_BYTES = HALO_F4 * 16;    // 24 KB
+template <bool HALF>
+__device__ __forceinline__ void st_face_tasks(const Geom& g, const unsigned char* sl, int dom, int s, float4* slots) {
+  const int mu = s >> 6, f = s & 63;
+  float4 v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = *face_slot(slots, mu, 0, k, f);
+  HalfSpinor<float> h, uh;
+  f4_to_half(v, h);
+  const SU3<float> u = StageT<HALF>::link(sl, mu, face_site(mu, 0, f));
+  su3_mul(u, h, uh);
+  if (mu == 3) {
+    const int tf = __ldg(g.tflag + dom);
+    if ((tf >> 6) & 1) scale_half(uh, (float)g.bc_t);
+    if ((tf >> 7) & 1) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float4* w = face_slot(slots, mu, 1, k, f);
+        const float4 t = *w;
+        const float sg = (float)g.bc_t;
+        *w = make_float4(sg * t.x, sg * t.y, sg * t.z, sg * t.w);
+      }
+    }
+  }
+  half_to_f4(uh, v);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) *face_slot(slots, mu, 0, k, f) = v[k];
 }
 
 template <int MU>
@@ -310,21 +392,8 @@ __device__ __forceinline__ void st_face_take(const float4* slots, int s, Spinor<
   }
 }
 
-// all 512 face hops of the domain, then each site's sum of its face slots
-template <bool HALF, typename SIO>
-__device__ __forceinline__ void st_surface(const Geom& g, const SIO& x, const unsigned char* links, int dom,
-                                           int rhs_off, int s, float4* slots, Spinor<float>& acc) {
-  const int w = s >> 5;
-  const int side = (w >> 1) & 1;
-  const int f = ((w & 1) << 5) | (s & 31);
-  if (w < 4) {
-    st_face_task<0, HALF>(g, x, links, dom, rhs_off, side, f, slots);
-    st_face_task<2, HALF>(g, x, links, dom, rhs_off, side, f, slots);
-  } else {
-    st_face_task<1, HALF>(g, x, links, dom, rhs_off, side, f, slots);
-    st_face_task<3, HALF>(g, x, links, dom, rhs_off, side, f, slots);
-  }
-  __syncthreads();
+// the slots of this thread's faces, summed into acc
+__device__ __forceinline__ void st_face_sum(const float4* slots, int s, Spinor<float>& acc) {
   st_face_take<0>(slots, s, acc);
   st_face_take<1>(slots, s, acc);
   st_face_take<2>(slots, s, acc);
@@ -363,7 +432,8 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   float4* sx = reinterpret_cast<float4*>(smem);                              // 24 KB
   unsigned char* sl = smem + SX_BYTES;                                        // links
   unsigned char* sc = sl + ST::LINK_BYTES;                                     // C_inv
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);  // staging copies
+  uint64_t* hbar = bar + 1;                                              // halo copy
   const Geom& g = a.g;
   if (loop_idle(g)) return;
   const int s = threadIdx.x;
@@ -374,6 +444,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (s == 0) {
     mbar_init(bar, 1);
+    mbar_init(hbar, 1);
     mbar_expect_tx(bar, ST::LINK_BYTES + ST::CLOV_BYTES + a.extra_tx);
     bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, bar);
     bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, bar);
@@ -385,26 +456,36 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
     const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
     const int rhs_off = r * g.ndom;
     if (r > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
+    if (a.do_surface && s == 0) {
+      // the halo lands in the slots (the start of the x buffer); order the
+      // earlier generic accesses to it before the asynchronous copy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(hbar, HALO_BYTES);
+      bulk_copy_g2s(sx, a.halo + (size_t)domr * HALO_F4, HALO_BYTES, hbar);
+    }
     Spinor<float> src;
     if (a.s_in32.p) a.s_in32.load(g, domr, s, src);
     else a.s_in.load(g, domr, s, src);
-    Spinor<float> acc;
-    zero(acc);
-    if (a.do_surface) st_surface<HALF>(g, a.x, a.links, dom, rhs_off, s, sx, acc);
-    if (r == 0) {
-      __syncthreads();  // barrier initialisation visible to every thread
-      const bool ok = mbar_wait_bounded(bar, 0);
-      if (__syncthreads_or(!ok)) {
+    if (r == 0) __syncthreads();  // barrier initialisation visible to every thread
+    {
+      const bool ok_st = r > 0 || mbar_wait_bounded(bar, 0);
+      const bool ok_h = !a.do_surface || mbar_wait_bounded(hbar, r & 1);
+      if (__syncthreads_or(!(ok_st && ok_h))) {
         // a wait gave up: record it, give the copies one more bounded wait and
         // leave (the decision is uniform across the CTA)
         if (s == 0) atomicExch(a.status, QCD_ERR_TIMEOUT);
-        if (!ok) mbar_wait_bounded(bar, 0);
+        if (!ok_st) mbar_wait_bounded(bar, 0);
+        if (!ok_h) mbar_wait_bounded(hbar, r & 1);
         return;
       }
-    } else if (a.do_surface) {
-      __syncthreads();  // every thread has taken its face slots before x overwrites them
     }
+    Spinor<float> acc;
     if (a.do_surface) {
+      st_face_tasks<HALF>(g, sl, dom, s, sx);
+      __syncthreads();
+      zero(acc);
+      st_face_sum(sx, s, acc);
+      __syncthreads();  // every thread has taken its face slots before x overwrites them
       st_clover<HALF>(sc, s, acc);
 #pragma unroll
       for (int sp = 0; sp < 4; ++sp)
@@ -455,6 +536,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
         a.s_out.store(g, domr, s, acc);
       }
     }
+    if (a.do_halo) st_halo_out<HALF>(g, sx, sl, a.halo, dom, rhs_off, s);  // sx holds the final iterate
     if (a.x_store) a.x.store(g, domr, s, xk);
     if (a.x_out32.p) a.x_out32.store(g, domr, s, xk);
   }
@@ -531,12 +613,11 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
 }
 
 // Algorithm 1 as 2 (n_sap + 1) launches.  s_first_in32 (float32) is the
-// first sweep's input, the source itself; x_out32, if set, receives the final
-// iterate in float32 (the last sweep of colour 0 also keeps x for the surface
-// term of the colour-1 launch that follows).
+// first sweep's input, the source itself.  The final iterate goes to x_out32
+// if it is set, else to x.  halo holds 96 bytes per site and right-hand side.
 template <bool HALF, typename SIO>
 static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b, F32Spinor x_out32,
-                            int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+                            float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
   StagedArgs<HALF, SIO> a;
   a.g = ctx->geom;
   a.nrhs = nrhs;
@@ -546,6 +627,7 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
   a.x = x;
   a.s_out = s;
   a.s_in = s;
+  a.halo = halo;
   a.links = (const unsigned char*)(HALF ? ctx->st_link16 : ctx->st_link32);
   a.clov = (const unsigned char*)(HALF ? ctx->st_clov16 : ctx->st_clov32);
   a.status = ctx->d_status;
@@ -561,7 +643,8 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
       a.do_surface = (sweep == 0 && colour == 0) ? 0 : 1;
       const bool last = sweep == n_sap;
       a.x_out32 = last ? x_out32 : F32Spinor{nullptr};
-      a.x_store = (!last || !x_out32.p || colour == 0) ? 1 : 0;
+      a.x_store = (last && !x_out32.p) ? 1 : 0;
+      a.do_halo = (last && colour == 1) ? 0 : 1;
       LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(ctx->geom.nhalf);
@@ -579,17 +662,18 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
   }
 }
 
-void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
-                             int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<false, F32Spinor>(ctx, s_first_in, s, x, b, F32Spinor{nullptr}, nrhs, n_sap, n_jac, st);
+void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b,
+                             float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+  staged_sequence<false, F32Spinor>(ctx, s_first_in, s, x, b, F32Spinor{nullptr}, halo, nrhs, n_sap, n_jac, st);
 }
-void sap_staged_sequence_f16(qcd_ctx* ctx, F32Spinor s_first_in, F16Spinor s, F16Spinor x, F32Spinor b,
-                             F32Spinor x_out, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<true, F16Spinor>(ctx, s_first_in, s, x, b, x_out, nrhs, n_sap, n_jac, st);
+void sap_staged_sequence_f16(qcd_ctx* ctx, F32Spinor s_first_in, F16Spinor s, F32Spinor b, F32Spinor x_out,
+                             float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+  staged_sequence<true, F16Spinor>(ctx, s_first_in, s, F16Spinor{nullptr, nullptr}, b, x_out, halo, nrhs, n_sap, n_jac,
+                                   st);
 }
-void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b, int nrhs,
-                              int n_sap, int n_jac, cudaStream_t st) {
-  staged_sequence<true, F32Spinor>(ctx, s_first_in, s, x, b, F32Spinor{nullptr}, nrhs, n_sap, n_jac, st);
+void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b,
+                              float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+  staged_sequence<true, F32Spinor>(ctx, s_first_in, s, x, b, F32Spinor{nullptr}, halo, nrhs, n_sap, n_jac, st);
 }
 
 }  // namespace qcd

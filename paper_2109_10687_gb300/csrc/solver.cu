@@ -138,7 +138,8 @@ static Workspace* workspace(qcd_ctx* ctx, int nrhs, bool solver) {
     double2** v64[] = {&w->x64, &w->r64, &w->b64, &w->t64};
     for (auto v : v64) QCD_CUDA_CHECK(cudaMalloc(v, b64));
     QCD_CUDA_CHECK(cudaMalloc(&w->sap_s, spinor_bytes(g, QCD_PREC_SINGLE) * keep_nrhs));
-    QCD_CUDA_CHECK(cudaMalloc(&w->sap_x16, spinor_bytes(g, QCD_PREC_HALF) * keep_nrhs));
+    // float16 x of the generic SAP kernel, or the shared-memory kernel's halo (96 B per site)
+    QCD_CUDA_CHECK(cudaMalloc(&w->sap_x16, spinor_bytes(g, QCD_PREC_SINGLE) * keep_nrhs));
     QCD_CUDA_CHECK(cudaMalloc(&w->sap_b16, spinor_bytes(g, QCD_PREC_HALF) * keep_nrhs));
   }
   return w;
