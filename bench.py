@@ -416,6 +416,17 @@ def main():
         info_fg = solve(P_FG)
     barrier()
     fg_ms = 1000.0 * (time.perf_counter() - tg) / nf
+    # the same solve with the residual of Algorithm 4 in double-float arithmetic
+    # on the float32 pipe instead of native float64 (an option, not the headline)
+    P_DF = params("half")
+    P_DF.residual_prec = 0
+    solve(P_DF)
+    barrier()
+    td = time.perf_counter()
+    for _ in range(nf):
+        info_df = solve(P_DF)
+    barrier()
+    df_ms = 1000.0 * (time.perf_counter() - td) / nf
 
     # Dslash: float32 D on the 32^4 field, CUDA events on the launching stream
     a32 = lat.field("single")
@@ -484,8 +495,11 @@ def main():
                        "true_resid": info_f32.true_resid, "speedup_of_mixed": f32_ms / graph_ms},
         "variants_ms": {"f16_all_graph_loop": graph_ms, "f16_links_clover_f32_vectors_graph_loop": hg_ms,
                         "f32_graph_loop": f32_ms, "f16_all_no_graph_events_per_launch": prof_ms,
-                        "f16_all_graph_loop_fgmres4_outer": fg_ms},
+                        "f16_all_graph_loop_fgmres4_outer": fg_ms,
+                        "f16_all_graph_loop_double_float_residual": df_ms},
         "fgmres4_outer": {"inner": info_fg.inner_iters, "outer": info_fg.outer_iters, "true_resid": info_fg.true_resid},
+        "double_float_residual": {"inner": info_df.inner_iters, "outer": info_df.outer_iters,
+                                  "true_resid": info_df.true_resid},
         "dslash": {"kernel": "dslash_kernel<float, D>", "ms": d_ms, "gbs": d_gbs, "gflops": d_gflops,
                    "bytes_per_site": D_BYTES_PER_SITE, "flop_per_site": D_FLOP_PER_SITE,
                    "frac_of_hbm": d_gbs / peak, "peak_gbs": peak, "peak_kind": peak_kind},

@@ -210,6 +210,15 @@ int qcd_apply_A_block(qcd_ctx* ctx, void* out, const void* in, int row, int col,
 int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac, int sap_prec,
                   int with_A, void* stream);
 
+/* qcd_sap_apply for nrhs stacked fields (in and out hold nrhs internal
+ * float32 fields one after the other).  With 4^4 domains every right-hand
+ * side goes through each block-kernel launch and shares its staged links and
+ * C_inv, as in the batched qcd_solve; each right-hand side's result is the
+ * one qcd_sap_apply gives for it alone.  1 <= nrhs <= 65535, else
+ * QCD_ERR_ARG. */
+int qcd_sap_apply_nrhs(qcd_ctx* ctx, void* out, const void* in, int nrhs, int n_sap, int n_jac, int sap_prec,
+                       int with_A, void* stream);
+
 /* ---- BLAS-1 (float32 internal fields, float64 results) --------------- */
 
 /* *result = |a|^2 (host pointer), accumulated per block in float32 and

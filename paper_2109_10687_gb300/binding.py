@@ -72,6 +72,7 @@ _SIGS = {
     "qcd_apply_clover": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "qcd_apply_A_block": (_I, [_P, _P, _P, _I, _I, _P]),
     "qcd_sap_apply": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
+    "qcd_sap_apply_nrhs": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P]),
     "qcd_norm2": (_I, [_P, ctypes.POINTER(_D), _P, _I, _I, _P]),
     "qcd_norm2_noalloc": (_I, [_P, ctypes.POINTER(_D), _P, _I, _I, _P]),
     "qcd_cdot": (_I, [_P, ctypes.POINTER(_D), _P, _P, _I, _I, _P]),
@@ -220,6 +221,11 @@ def qcd_apply_A_block(ctx, out, inp, row, col, stream=None):
 def qcd_sap_apply(ctx, out, inp, n_sap, n_jac, sap_prec=PREC_SINGLE, with_A=0, stream=None):
     return check(ctx, lib().qcd_sap_apply(ctx, _ptr(out), _ptr(inp), int(n_sap), int(n_jac), int(sap_prec),
                                           int(with_A), _stream(stream)))
+
+
+def qcd_sap_apply_nrhs(ctx, out, inp, nrhs, n_sap, n_jac, sap_prec=PREC_SINGLE, with_A=0, stream=None):
+    return check(ctx, lib().qcd_sap_apply_nrhs(ctx, _ptr(out), _ptr(inp), int(nrhs), int(n_sap), int(n_jac),
+                                               int(sap_prec), int(with_A), _stream(stream)))
 
 
 def qcd_norm2(ctx, a, prec=PREC_SINGLE, nrhs=1, stream=None):

@@ -882,24 +882,30 @@ extern "C" int qcd_solve_params_default(qcd_solve_params* p) {
   return QCD_OK;
 }
 
-extern "C" int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac, int sap_prec, int with_A,
-                             void* stream) {
+extern "C" int qcd_sap_apply_nrhs(qcd_ctx* ctx, void* out, const void* in, int nrhs, int n_sap, int n_jac,
+                                  int sap_prec, int with_A, void* stream) {
   if (!ctx) return QCD_ERR_ARG;
   API_BEGIN
   require_operator(ctx);
   QCD_REQUIRE(out && in && out != in, QCD_ERR_ARG, "qcd_sap_apply: bad buffers");
+  QCD_REQUIRE(nrhs >= 1 && nrhs <= 65535, QCD_ERR_ARG, "qcd_sap_apply: 1 <= nrhs <= 65535");
   QCD_REQUIRE(n_sap >= 0 && n_jac >= 1, QCD_ERR_ARG, "qcd_sap_apply: n_sap >= 0 and n_jac >= 1");
   QCD_REQUIRE(sap_prec == QCD_PREC_SINGLE || sap_prec == QCD_PREC_HALF || sap_prec == QCD_PREC_HALF_GAUGE,
               QCD_ERR_ARG, "qcd_sap_apply: sap_prec must be SINGLE, HALF or HALF_GAUGE");
   cudaStream_t st = (cudaStream_t)stream;
-  Workspace* w = workspace(ctx, 1, true);
+  Workspace* w = workspace(ctx, nrhs, true);
   if (with_A) {
-    am_sap(ctx, w, w->tmp32, (float4*)out, (const float4*)in, 1, n_sap, n_jac, sap_prec, st);
+    am_sap(ctx, w, w->tmp32, (float4*)out, (const float4*)in, nrhs, n_sap, n_jac, sap_prec, st);
   } else {
-    sap_apply_launch(ctx, (float4*)out, (const float4*)in, 1, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16,
+    sap_apply_launch(ctx, (float4*)out, (const float4*)in, nrhs, n_sap, n_jac, sap_prec, w->sap_s, w->sap_x16,
                      w->sap_b16, st);
   }
   API_END(ctx)
+}
+
+extern "C" int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac, int sap_prec, int with_A,
+                             void* stream) {
+  return qcd_sap_apply_nrhs(ctx, out, in, 1, n_sap, n_jac, sap_prec, with_A, stream);
 }
 
 extern "C" int qcd_norm2(qcd_ctx* ctx, double* result, const void* a, int prec, int nrhs, void* stream) {

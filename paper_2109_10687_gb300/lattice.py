@@ -100,11 +100,14 @@ class Lattice:
         B.qcd_apply_A_block(self.ctx, o, a, row, col)
         return self.to_canonical(o, "single")
 
-    def sap(self, psi, n_sap, n_jac, sap_prec="single", with_A=False):
-        a = self.to_internal(psi, "single")
-        o = self.field("single")
-        B.qcd_sap_apply(self.ctx, o, a, n_sap, n_jac, PREC[sap_prec], int(with_A))
-        return self.to_canonical(o, "single")
+    def sap(self, psi, n_sap, n_jac, sap_prec="single", with_A=False, nrhs=1):
+        a = self.to_internal(psi, "single", nrhs)
+        o = self.field("single", nrhs)
+        if nrhs == 1:
+            B.qcd_sap_apply(self.ctx, o, a, n_sap, n_jac, PREC[sap_prec], int(with_A))
+        else:
+            B.qcd_sap_apply_nrhs(self.ctx, o, a, nrhs, n_sap, n_jac, PREC[sap_prec], int(with_A))
+        return self.to_canonical(o, "single", nrhs)
 
     def solve(self, b, nrhs=1, params=None, raise_on_error=True, host=False, **kw):
         """x with D x = b (canonical complex128 in, canonical complex128 out)."""
