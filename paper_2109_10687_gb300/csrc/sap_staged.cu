@@ -374,21 +374,46 @@ __device__ __forceinline__ void st_face_tasks(const Geom& g, const unsigned char
   for (int k = 0; k < 3; ++k) *face_slot(slots, mu, 0, k, f) = v[k];
 }
 
+// acc += the slot of this site's face in direction MU, without branches.  In
+// a 4^4 domain a site has at most one face per direction: c_MU = 3 (side 0,
+// forward hop, rebuilt with 1 - gamma_MU) or c_MU = 0 (side 1, backward hop,
+// 1 + gamma_MU).  The rebuild is written as the side-1 form with the lower
+// spins scaled by sg = -1 for side 0 (the two forms differ only there), and
+// a site with no face in MU reads some slot and adds it with weight w = 0.
+// With w and sg equal to +-1 or 0 every fma is an exact addition.
 template <int MU>
 __device__ __forceinline__ void st_face_take(const float4* slots, int s, Spinor<float>& acc) {
   const int c = lc<MU>(s);
-  if (c == 3 || c == 0) {
-    const int side = c == 0;
-    const int f = face_index(MU, s);
-    HalfSpinor<float> uh;
+  const int side = c == 0;
+  const float w = (c == 0 || c == 3) ? 1.0f : 0.0f;
+  const float sg = side ? w : -w;
+  const int f = face_index(MU, s);
+  HalfSpinor<float> uh;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float4 v = *face_slot(const_cast<float4*>(slots), MU, side, k, f);
-      uh.h[(2 * k) / 3][(2 * k) % 3] = make_cx(v.x, v.y);
-      uh.h[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v.z, v.w);
+  for (int k = 0; k < 3; ++k) {
+    const float4 v = *face_slot(const_cast<float4*>(slots), MU, side, k, f);
+    uh.h[(2 * k) / 3][(2 * k) % 3] = make_cx(v.x, v.y);
+    uh.h[(2 * k + 1) / 3][(2 * k + 1) % 3] = make_cx(v.z, v.w);
+  }
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    const cx<float> h0 = uh.h[0][col], h1 = uh.h[1][col];
+    acc.v[0][col] = cfma(w, h0, acc.v[0][col]);
+    acc.v[1][col] = cfma(w, h1, acc.v[1][col]);
+    // spins 2 and 3 of the (1 + gamma_MU) rebuild (accumulate1 with PM = +1)
+    if (MU == 0) {
+      acc.v[2][col] = cfma(sg, times_i(h1), acc.v[2][col]);
+      acc.v[3][col] = cfma(sg, times_i(h0), acc.v[3][col]);
+    } else if (MU == 1) {
+      acc.v[2][col] = cfma(sg, h1, acc.v[2][col]);
+      acc.v[3][col] = cfma(-sg, h0, acc.v[3][col]);
+    } else if (MU == 2) {
+      acc.v[2][col] = cfma(sg, times_i(h0), acc.v[2][col]);
+      acc.v[3][col] = cfma(sg, times_mi(h1), acc.v[3][col]);
+    } else {
+      acc.v[2][col] = cfma(sg, h0, acc.v[2][col]);
+      acc.v[3][col] = cfma(sg, h1, acc.v[3][col]);
     }
-    if (side == 0) accumulate<MU, -1>(acc, uh);
-    else accumulate<MU, +1>(acc, uh);
   }
 }
 
