@@ -42,30 +42,32 @@ D_BYTES_PER_SITE = 96 + 96 + 4 * 72 + 288          # in + out spinor, 4 links (1
 D_FLOP_PER_SITE = 1824
 
 
-def sap_bytes_per_site(prec):
-    """Algorithmic bytes per site of one SAP half-sweep launch, averaged over
-    the launches of one M_SAP (n_sap + 1 sweeps, two colours): read s (the
-    float32 source in the first sweep), the domain's links and C_inv, and
-    with a surface term the domain's halo (one float32 half spinor per hop
-    that enters the domain: 2 per site for 4^4 domains, 96 B); write the halo
-    of the other colour's domains (96 B, all but the last launch); then
-    either the residual update (read b in float32, write s) or, in the last
-    sweep, the float32 result x."""
+def sap_bytes_per_launch(prec, sweep, colour):
+    """Algorithmic bytes per site of the SAP half-sweep launch (sweep, colour)
+    of one M_SAP (n_sap + 1 sweeps, two colours): read s (the float32 source
+    in the first sweep), the domain's links and C_inv, and with a surface
+    term the domain's halo (one float32 half spinor per hop that enters the
+    domain: 2 per site for 4^4 domains, 96 B); write the halo of the other
+    colour's domains (96 B, all but the last launch); then either the residual
+    update (read b in float32, write s) or, in the last sweep, the float32
+    result x."""
     sp = 96 if prec == "single" else 52
     link = 72 if prec == "single" else 36
     clov = 288 if prec == "single" else 144
     halo = 96
-    seq = []
-    for sweep in range(N_SAP + 1):
-        last = sweep == N_SAP
-        for colour in (0, 1):
-            nb = (96 if sweep == 0 else sp) + 4 * link + clov
-            if not (sweep == 0 and colour == 0):
-                nb += halo                       # halo in
-            if not (last and colour == 1):
-                nb += halo                       # halo out
-            nb += 96 if last else 96 + sp        # x out, or b in and s out
-            seq.append(nb)
+    last = sweep == N_SAP
+    nb = (96 if sweep == 0 else sp) + 4 * link + clov
+    if not (sweep == 0 and colour == 0):
+        nb += halo                       # halo in
+    if not (last and colour == 1):
+        nb += halo                       # halo out
+    nb += 96 if last else 96 + sp        # x out, or b in and s out
+    return nb
+
+
+def sap_bytes_per_site(prec):
+    """sap_bytes_per_launch averaged over the launches of one M_SAP."""
+    seq = [sap_bytes_per_launch(prec, sweep, colour) for sweep in range(N_SAP + 1) for colour in (0, 1)]
     return sum(seq) / len(seq)
 
 

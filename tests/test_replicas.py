@@ -77,3 +77,16 @@ def test_reference_arm_line_contract():
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_sap_byte_model_matches_the_profiled_launch():
+    """The SAP kernel's algorithmic bytes per site: the launch type that the
+    ncu summary profiles (second sweep, E colour: float16 s in and out, links
+    and C_inv, halo in and out, float32 b) is 680 B; the first launch has no
+    halo in and reads the float32 source; the last writes no halo and the
+    float32 result instead of the update."""
+    import bench
+    assert bench.sap_bytes_per_launch("half", 1, 0) == 52 + 144 + 144 + 96 + 96 + 96 + 52 == 680
+    assert bench.sap_bytes_per_launch("half", 0, 0) == 96 + 288 + 96 + 148
+    assert bench.sap_bytes_per_launch("half", bench.N_SAP, 1) == 52 + 288 + 96 + 96
+    assert abs(bench.sap_bytes_per_site("half") - 659.2) < 1e-9
