@@ -6,12 +6,13 @@
 // One CTA per domain, one thread per site, the domain shape fixed at compile
 // time (strides 1, 4, 16, 64).  At entry one thread arms an mbarrier and
 // issues two cp.async.bulk copies: the domain's links and its C_inv, each a
-// contiguous block of a staging layout built for this kernel.  While they
-// are in flight the threads read their s and the domain's halo; they then
-// wait (bounded) on the barrier and run every Jacobi sweep and the residual
-// update from shared memory.  The launches of one M_SAP use programmatic
-// dependent launch: the staging copies are issued before the kernel waits
-// for the previous launch.
+// contiguous block of a staging layout built for this kernel.  The launches
+// of one M_SAP use programmatic dependent launch: these copies are issued
+// before the kernel waits for the previous launch.  After that wait the
+// same thread issues a third copy, the domain's halo block (below), and the
+// threads read their s; they then wait (bounded) on the copies and run the
+// surface term, every Jacobi sweep and the residual update from shared
+// memory.
 //
 // Halo.  The surface term of a colour-c launch needs, for each hop that
 // enters the domain, U P x of the neighbouring (other-colour) domain's
@@ -20,8 +21,9 @@
 // its face sites it writes the half spinor the neighbour needs into the
 // neighbour's halo slots, U^dag P+ x for a backward hop (complete) and P- x
 // for a forward hop (the receiver multiplies by its own link U, which it has
-// staged).  The receiving launch reads its halo with coalesced loads and no
-// neighbour lookups.  This is the exchange of Sec. 4.1, done through memory.
+// staged).  The receiving launch brings its halo block in with one bulk copy
+// and needs no neighbour lookups.  This is the exchange of Sec. 4.1, done
+// through memory.
 //
 //   staging layouts per domain (global = shared):
 //     links  f16: __half2 [mu 4][site 256][10]    40 B per link (9 + pad), 8-byte reads
