@@ -355,8 +355,10 @@ int qcd_device_status(qcd_ctx* ctx, int* status, int reset, void* stream);
  * QCD_INJECT_NONE clears; QCD_INJECT_STAGING_WAIT makes the SAP block
  * kernel's staging wait expect 16 bytes more than its copies bring, so the
  * bounded wait runs out (about a second) and the kernel records
- * QCD_ERR_TIMEOUT.  No GPU fault is involved. */
-enum { QCD_INJECT_NONE = 0, QCD_INJECT_STAGING_WAIT = 1 };
+ * QCD_ERR_TIMEOUT; QCD_INJECT_HALO_WAIT does the same to its wait for the
+ * face-halo copy (launches with a surface term).  No GPU fault is
+ * involved. */
+enum { QCD_INJECT_NONE = 0, QCD_INJECT_STAGING_WAIT = 1, QCD_INJECT_HALO_WAIT = 2 };
 int qcd_test_inject(qcd_ctx* ctx, int what);
 
 /* Measurement utility (no counterpart in the paper): the device's float32

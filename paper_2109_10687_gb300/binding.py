@@ -301,6 +301,7 @@ def qcd_measure_fp32_peak(ctx, stream=None):
 
 INJECT_NONE = 0
 INJECT_STAGING_WAIT = 1
+INJECT_HALO_WAIT = 2
 
 
 def qcd_device_status(ctx, reset=False, stream=None):

@@ -601,7 +601,7 @@ extern "C" int qcd_device_status(qcd_ctx* ctx, int* status, int reset, void* str
 }
 
 extern "C" int qcd_test_inject(qcd_ctx* ctx, int what) {
-  if (!ctx || what < QCD_INJECT_NONE || what > QCD_INJECT_STAGING_WAIT) return QCD_ERR_ARG;
+  if (!ctx || what < QCD_INJECT_NONE || what > QCD_INJECT_HALO_WAIT) return QCD_ERR_ARG;
   ctx->inject = what;
   return QCD_OK;
 }

@@ -125,6 +125,7 @@ struct StagedArgs {
   const unsigned char* clov;
   int* status;                 // word 0: set to QCD_ERR_TIMEOUT if a wait gives up
   int extra_tx;                // testing: bytes the staging wait expects beyond its copies
+  int extra_htx;               // testing: bytes the halo wait expects beyond its copy
 };
 
 // ---------------------------------------------------------------------------
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
       // the halo lands in the slots (the start of the x buffer); order the
       // earlier generic accesses to it before the asynchronous copy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(hbar, HALO_BYTES);
+      mbar_expect_tx(hbar, HALO_BYTES + a.extra_htx);
       bulk_copy_g2s(sx, a.halo + (size_t)domr * HALO_F4, HALO_BYTES, hbar);
     }
     Spinor<float> src;
@@ -661,6 +662,7 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
   // test hook: wait for 16 bytes that no copy brings, so that the bounded
   // wait gives up and reports QCD_ERR_TIMEOUT
   a.extra_tx = ctx->inject == QCD_INJECT_STAGING_WAIT ? 16 : 0;
+  a.extra_htx = ctx->inject == QCD_INJECT_HALO_WAIT ? 16 : 0;
   const int smem = SX_BYTES + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 16;
   for (int sweep = 0; sweep <= n_sap; ++sweep) {
     a.s_in32 = sweep == 0 ? s_first_in32 : F32Spinor{nullptr};

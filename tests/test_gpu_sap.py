@@ -129,3 +129,21 @@ def test_staging_wait_timeout_is_reported_and_context_survives():
         assert rel_l2(got, sap.msap(p.op, b, 4, 4)) <= 5e-3
     finally:
         p.close()
+
+
+def test_halo_wait_timeout_is_reported_and_context_survives():
+    """The same failure path for the wait on the face-halo copy, which only
+    launches with a surface term make (here the O half-sweep)."""
+    from paper_2109_10687_gb300 import binding as B
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), eps=0.3, kappa=0.12, csw=1.0, seed=1101)
+    try:
+        b = p.source(2107)
+        B.qcd_test_inject(p.lat.ctx, B.INJECT_HALO_WAIT)
+        p.lat.sap(b, 0, 1, "half_gauge")
+        assert B.qcd_device_status(p.lat.ctx, reset=True) == B.QCD_ERR_TIMEOUT
+        B.qcd_test_inject(p.lat.ctx, B.INJECT_NONE)
+        got = to_np(p.lat.sap(b, 4, 4, "half_gauge"))
+        assert B.qcd_device_status(p.lat.ctx) == B.QCD_OK
+        assert rel_l2(got, sap.msap(p.op, b, 4, 4)) <= 5e-3
+    finally:
+        p.close()
