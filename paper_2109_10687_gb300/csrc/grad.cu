@@ -44,10 +44,14 @@ __device__ __forceinline__ M3f dg(const M3f& a) {
 
 __device__ __forceinline__ void coords_of(const Geom& g, long long n, int x[4]) { site_coords(g, n, x); }
 
+// periodic wrap of a coordinate at most one period outside [0, L)
+__device__ __forceinline__ int wrap1(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+// internal (domain, site) of x + off, |off_k| <= 1
 __device__ __forceinline__ void at_coords(const Geom& g, const int x[4], const int off[4], int& dom, int& s) {
   int y[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) y[k] = (x[k] + off[k] + 2 * g.L[k]) % g.L[k];
+  for (int k = 0; k < 4; ++k) y[k] = wrap1(x[k] + off[k], g.L[k]);
   coords_to_internal(g, y, dom, s);
 }
 
@@ -139,11 +143,9 @@ __device__ __forceinline__ M3f load_v(const Geom& g, const float2* V, int p, lon
   return r;
 }
 
-__device__ __forceinline__ long long canon_index(const Geom& g, const int x[4], const int off[4]) {
-  int y[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) y[k] = (x[k] + off[k] + 2 * g.L[k]) % g.L[k];
-  return ((long long)(y[3] * g.L[2] + y[2]) * g.L[1] + y[1]) * g.L[0] + y[0];
+// canonical index of the coordinates x (each in [0, L))
+__device__ __forceinline__ long long canon_index(const Geom& g, const int x[4]) {
+  return ((long long)(x[3] * g.L[2] + x[2]) * g.L[1] + x[1]) * g.L[0] + x[0];
 }
 
 template <int MU>
@@ -215,9 +217,10 @@ __global__ void __launch_bounds__(128) force_kernel(Geom g, F32Spinor xs, F32Spi
           int base[4] = {0, 0, 0, 0};
           base[mu] -= fk.om;
           base[nu] -= fk.on;
-          const long long nn = canon_index(g, y, base);
           int xn[4];
-          coords_of(g, nn, xn);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xn[q] = wrap1(y[q] + base[q], g.L[q]);
+          const long long nn = canon_index(g, xn);
           // R_k = A_{k+1} .. A_4 V A_1 .. A_{k-1}
           M3f r;
           for (int i = 0; i < 3; ++i)
