@@ -186,10 +186,12 @@ __device__ void hop_force(const Geom& g, const F32Spinor& xs, const F32Spinor& l
 __global__ void __launch_bounds__(128) force_kernel(Geom g, F32Spinor xs, F32Spinor ls, LinkPtr<float> U,
                                                     const float2* V, float kappa, int with_clover, int project,
                                                     double* out) {
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= g.vol * 4) return;
-  const int d = (int)(gid & 3);
-  const long long n = gid >> 2;
+  // a block takes 32 sites, warp d their links in direction d: the
+  // direction, and with it every branch and loop bound below, is uniform
+  // across a warp
+  const int d = threadIdx.x >> 5;
+  const long long n = blockIdx.x * 32LL + (threadIdx.x & 31);
+  if (n >= g.vol) return;
   int y[4];
   coords_of(g, n, y);
   int dom, s;
@@ -375,7 +377,7 @@ extern "C" int qcd_grad(qcd_ctx* ctx, const double* eta, const double* b, const 
       }
       {
         LaunchScope ls_(ctx, QCD_KC_OTHER, st);
-        force_kernel<<<grid_for(g.vol * 4, 128), 128, 0, st>>>(g, F32Spinor{x32}, F32Spinor{l32},
+        force_kernel<<<grid_for(g.vol, 32), 128, 0, st>>>(g, F32Spinor{x32}, F32Spinor{l32},
                                                               LinkPtr<float>{ctx->u32}, V, (float)ctx->kappa,
                                                               with_clover, project, grad_U);
         check_launch();
