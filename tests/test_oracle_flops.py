@@ -33,3 +33,15 @@ def test_per_site_counts():
     assert flops.f_in((4, 4, 4, 4), h) == 1608
     assert flops.f_out((4, 4, 4, 4), h) * 2 == 1797
     assert flops.D_FLOP_PER_SITE == 1320 + 504
+
+
+def test_benchmark_restates_the_oracle_flop_model():
+    """bench_configs restates the per-site flop model (it may not import the
+    oracle outside the CPU-baseline leg); the two agree for cubic, elongated
+    and the paper's own domain shapes."""
+    import bench_configs
+    h = (168, 168, 168, 168)
+    for domain in ((4, 4, 4, 4), (16, 4, 2, 2), (8, 4, 4, 2), (16, 6, 4, 3), (16, 12, 8, 12)):
+        for n_sap, n_jac in ((4, 2), (4, 4), (0, 1)):
+            got = bench_configs._paper_flop_per_site_iter(domain, n_sap, n_jac, h)
+            assert abs(got - flops.flop_per_site_iter(domain, n_sap, n_jac, h)) < 1e-9, (domain, n_sap, n_jac)
