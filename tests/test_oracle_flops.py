@@ -45,3 +45,22 @@ def test_benchmark_restates_the_oracle_flop_model():
         for n_sap, n_jac in ((4, 2), (4, 4), (0, 1)):
             got = bench_configs._paper_flop_per_site_iter(domain, n_sap, n_jac, h)
             assert abs(got - flops.flop_per_site_iter(domain, n_sap, n_jac, h)) < 1e-9, (domain, n_sap, n_jac)
+
+
+def test_sap_kernel_flop_count_uses_the_oracle_constants():
+    """The roofline's flop count of the SAP block kernel (bench.sap_flop_per_site)
+    is built from the oracle's per-site constants for 4^4 domains: f_in per
+    A_cc application (n_jac Jacobi sweeps plus one for the residual update, 48
+    for the update itself) and f_out for the surface term, averaged over the
+    2 (n_sap + 1) launches of M_SAP."""
+    import bench
+    h = (168, 168, 168, 168)
+    fi, fo = flops.f_in((4, 4, 4, 4), h), flops.f_out((4, 4, 4, 4), h)
+    seq = []
+    for sweep in range(bench.N_SAP + 1):
+        for colour in (0, 1):
+            surf = fo if not (sweep == 0 and colour == 0) else 0.0
+            upd = fi + 48 if sweep < bench.N_SAP else 0.0
+            seq.append(surf + bench.N_JAC * fi + upd)
+    assert abs(bench.sap_flop_per_site() - sum(seq) / len(seq)) < 1e-9
+    assert abs(bench.sap_flop_per_site() - 8565.45) < 1e-9
