@@ -64,3 +64,12 @@ def test_sap_kernel_flop_count_uses_the_oracle_constants():
             seq.append(surf + bench.N_JAC * fi + upd)
     assert abs(bench.sap_flop_per_site() - sum(seq) / len(seq)) < 1e-9
     assert abs(bench.sap_flop_per_site() - 8565.45) < 1e-9
+
+
+def test_dslash_roofline_constants():
+    """The Dslash roofline counts 1824 flop (the oracle's) and 768 bytes per
+    site: spinor in and out (2 x 96), four float32 links of 18 reals (288)
+    and the two float32 clover blocks of 36 reals (288)."""
+    import bench
+    assert bench.D_FLOP_PER_SITE == flops.D_FLOP_PER_SITE
+    assert bench.D_BYTES_PER_SITE == 2 * 24 * 4 + 4 * 18 * 4 + 2 * 36 * 4 == 768
