@@ -16,11 +16,13 @@ def norm2(a):
     return float(np.vdot(a.ravel(), a.ravel()).real)
 
 
-def bicgstab(apply, b, tol, maxiter, x0=None):
+def bicgstab(apply, b, tol, maxiter, x0=None, record=None):
     """Textbook BiCGStab for apply(x) = b with r~ = r_0; float64.
 
     Returns (x, iterations, converged).  This is the reference solution of
     D x = b against which every preconditioned solve is compared.
+    ``record`` (a list) receives (alpha, omega, x, r) per iteration when
+    given.
     """
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - apply(x)
@@ -43,6 +45,8 @@ def bicgstab(apply, b, tol, maxiter, x0=None):
         x = x + alpha * p + omega * s
         r = s - omega * t
         rho_old = rho
+        if record is not None:
+            record.append((alpha, omega, x.copy(), r.copy()))
         if np.sqrt(norm2(r)) / bn < tol:
             return x, it, True
     return x, maxiter, False

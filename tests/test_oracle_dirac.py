@@ -7,7 +7,7 @@ import pytest
 from lattice_inputs import gaussian_spinor, random_su3_field, random_su3_sites
 from oracle import dense
 from oracle.dirac import CloverWilson, dag, field_strength, site_mul, spin_mul
-from oracle.gamma import PLANES, chiral_rotation, gamma5, gamma_chiral, gamma_paper, sigma
+from oracle.gamma import PLANES, chiral_rotation, gamma5, gamma_chiral, gamma_paper
 
 
 def free_links(dims):
@@ -162,7 +162,9 @@ def test_constant_abelian_field_closed_form(basis):
     expect12 = -1j * np.diag(np.sin(bmag * tdiag))
     assert np.allclose(f[..., 0, :, :], expect12, atol=1e-14)
     assert np.abs(f[..., 1:, :, :]).max() < 1e-14
-    c_expect = kappa * csw * np.kron(np.diag(np.sin(bmag * tdiag)), sigma(g, 0, 1))
+    # sigma_12 = i g1 g2 = diag(-1, 1, -1, 1), written out by hand (equal in both bases)
+    sigma12 = np.diag([-1.0, 1.0, -1.0, 1.0])
+    c_expect = kappa * csw * np.kron(np.diag(np.sin(bmag * tdiag)), sigma12)
     assert np.allclose(op.c, c_expect, atol=1e-14)
 
 

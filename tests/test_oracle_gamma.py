@@ -51,3 +51,30 @@ def test_chiral_basis_form():
     for k in range(3):
         expect = np.block([[z, -1j * pauli[k]], [1j * pauli[k], z]])
         assert np.allclose(g[k], expect)
+
+
+def test_sigma_squares_to_one():
+    """sigma_{mu nu}^2 = 1 for mu != nu: with anticommuting gammas,
+    [g_mu, g_nu] = 2 g_mu g_nu and (i g_mu g_nu)^2 = -g_mu g_nu g_mu g_nu = 1.
+    This fixes the factor i/2 of App. A (a factor 1 would give 4)."""
+    for basis in (gamma_paper, gamma_chiral):
+        g = basis()
+        for mu, nu in PLANES:
+            s = sigma(g, mu, nu)
+            assert np.allclose(s @ s, np.eye(4), atol=1e-15)
+
+
+def test_sigma_hand_written_entries():
+    """sigma_12 = i g1 g2 and sigma_34 = i g3 g4 multiplied out by hand from
+    the printed App. A matrices: g1 g2 = diag(i, -i, i, -i), so
+    sigma_12 = diag(-1, 1, -1, 1) (the same in the chiral basis, which
+    rotates the two equal 2x2 blocks onto each other); sigma_34 couples the
+    upper and lower spin pairs through diag(1, -1), and becomes
+    diag(1, -1, -1, 1) in the chiral basis."""
+    s12 = np.diag([-1.0, 1.0, -1.0, 1.0])
+    s34_paper = np.array([[0, 0, 1, 0], [0, 0, 0, -1], [1, 0, 0, 0], [0, -1, 0, 0]], dtype=float)
+    s34_chiral = np.diag([1.0, -1.0, -1.0, 1.0])
+    assert np.allclose(sigma(gamma_paper(), 0, 1), s12, atol=1e-15)
+    assert np.allclose(sigma(gamma_chiral(), 0, 1), s12, atol=1e-15)
+    assert np.allclose(sigma(gamma_paper(), 2, 3), s34_paper, atol=1e-15)
+    assert np.allclose(sigma(gamma_chiral(), 2, 3), s34_chiral, atol=1e-15)

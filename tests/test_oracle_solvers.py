@@ -133,3 +133,52 @@ def test_maxiter_exhaustion_reports_status():
     b = gaussian_spinor(dims, 152)
     _, _, it, status = solvers.bicgstab_precdd(op, op.apply_cinv(b), 0, 1, 1e-14, 2)
     assert status == "maxiter" and it == 2
+
+
+def test_algorithm5_iterates_equal_textbook_bicgstab(monkeypatch):
+    """Algorithm 5 is BiCGStab on the right-preconditioned operator A M_SAP
+    with r~ = b and x_0 = 0 (Sec. 3).  In exact arithmetic its iterates are
+    those of the independently written textbook BiCGStab on the same
+    operator (r~ = r_0 = b there too), step for step: the same alpha, omega,
+    x and r.  A wrong beta, omega or update in either would part them from
+    the second iteration on.  After each omega step the new residual is
+    orthogonal to t = (A M_SAP) s, which is what omega minimises."""
+    from oracle import sap
+    dims = (4, 4, 4, 8)
+    g = gamma_chiral()
+    op = CloverWilson(random_su3_field(dims, 0.3, 161), 0.12, 1.0, g, domain=(2, 2, 2, 2))
+    b = op.apply_cinv(gaussian_spinor(dims, 162))
+    n_sap, n_jac, k = 1, 2, 4
+    am = lambda v: sap.am_sap(op, v, n_sap, n_jac)
+    ref = []
+    solvers.bicgstab(am, b, 0.0, k, record=ref)
+    assert len(ref) == k
+
+    calls = []
+    orig = sap.am_sap
+
+    def spy(op_, v, ns, nj):
+        out = orig(op_, v, ns, nj)
+        calls.append((v.copy(), out.copy()))
+        return out
+
+    monkeypatch.setattr(sap, "am_sap", spy)
+    rec = []
+    _, y, it, status = solvers.bicgstab_precdd(op, b, n_sap, n_jac, 0.0, k, record=rec)
+    monkeypatch.setattr(sap, "am_sap", orig)
+    assert status == "maxiter" and it == k and len(rec) == k
+    bn = np.linalg.norm(b.ravel())
+    for i in range(k):
+        alpha, omega, rnorm2 = rec[i]
+        a_ref, o_ref, x_ref, r_ref = ref[i]
+        assert abs(alpha - a_ref) <= 1e-10 * abs(a_ref)
+        assert abs(omega - o_ref) <= 1e-10 * abs(o_ref)
+        assert abs(np.sqrt(rnorm2) - np.linalg.norm(r_ref.ravel())) <= 1e-9 * bn
+        # the omega step: t = (A M) s, r_new = s - omega t, <t | r_new> = 0
+        s_vec, t_vec = calls[2 * i + 1]
+        r_new = s_vec - omega * t_vec
+        assert abs(np.vdot(t_vec.ravel(), r_new.ravel())) <= 1e-12 * np.linalg.norm(t_vec) * bn
+        assert abs(np.linalg.norm(r_new.ravel()) - np.linalg.norm(r_ref.ravel())) <= 1e-9 * bn
+    # the last iterate y (before x = M_SAP y) is the textbook x
+    x_ref = ref[-1][2]
+    assert np.linalg.norm((y - x_ref).ravel()) <= 1e-9 * np.linalg.norm(x_ref.ravel())
