@@ -28,6 +28,13 @@ import torch
 from bench import D_BYTES_PER_SITE, D_FLOP_PER_SITE, ClockSampler, measured_peaks
 
 
+def _smi_index():
+    """nvidia-smi index of cuda:0 (the first visible device)."""
+    import os
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    return vis.split(",")[0] if vis else "0"
+
+
 def _lat(dims, eps, kappa, csw, seed, domain=(4, 4, 4, 4)):
     from lattice_inputs import random_su3_field, random_su3_field_fast
     from paper_2109_10687_gb300.lattice import Lattice
@@ -99,50 +106,86 @@ def c1(args):
             "metric": "time to relative residual 1e-6", "unit": "ms", "results": res}
 
 
-def c3(args):
+def per_rhs_resid(lat, x, b, nrhs):
+    """|b_i - D x_i| / |b_i| for each right-hand side, with the library's
+    float64 D (canonical device fields in, one right-hand side at a time)."""
+    from paper_2109_10687_gb300 import binding as B
+    xi, dxi = lat.field("double"), lat.field("double")
+    out = []
+    for i in range(nrhs):
+        B.qcd_import_spinor(lat.ctx, xi, x[i].contiguous(), B.PREC_DOUBLE)
+        B.qcd_apply_D(lat.ctx, dxi, xi, B.PREC_DOUBLE)
+        dx = torch.empty_like(b[i])
+        B.qcd_export_spinor(lat.ctx, dx, dxi, B.PREC_DOUBLE)
+        out.append(float(torch.linalg.vector_norm(b[i] - dx) / torch.linalg.vector_norm(b[i])))
+    del xi, dxi
+    return out
+
+
+def north_star_48x4(reps=1, f32_vectors=False):
+    """48^4, eps 0.25, kappa 0.125, c_SW 1.1, the 12 spin-colour point sources
+    at the origin, to float64 true residual 1e-10, three ways on one GPU:
+    one batched mixed-precision solve (float16-storage SAP, float32
+    BiCGStab, float64 defect correction; all right-hand sides through every
+    launch, the inner loop one graph), 12 sequential mixed-precision solves
+    (the same precision without batching), and 12 sequential plain float32
+    solves (float32 SAP; the comparison arm).  The ratio of the first two is
+    the batching gain, of the last two the precision gain."""
     from lattice_inputs import point_source
     from paper_2109_10687_gb300 import binding as B
     dims = (48, 48, 48, 48)
+    t_setup = time.perf_counter()
     lat = _lat(dims, 0.25, 0.125, 1.1, 1301)
     srcs = np.stack([point_source(dims, c, s) for c in range(3) for s in range(4)])
     b = torch.view_as_real(torch.from_numpy(srcs)).cuda().contiguous()
+    del srcs
     x = torch.zeros_like(b)
+    t_setup = time.perf_counter() - t_setup
     out = {}
-    clk = ClockSampler("0")
+    clk = ClockSampler(_smi_index())
     clk.start()
-    # warm (allocations, tuning) then time the batched mixed solve: float16
-    # links, C_inv and vectors in the SAP (the storage of the 32^4 benchmark line)
-    B.qcd_solve(lat.ctx, x, b, 12, _params("half"))
-    t_batch, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 12, _params("half")), 1)
+    B.qcd_solve(lat.ctx, x, b, 12, _params("half"))        # warm: allocations, tuning, graph
+    t_batch, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 12, _params("half")), reps)
+    res = per_rhs_resid(lat, x, b, 12)
     out["batched_mixed"] = {"s": t_batch, "inner": info.inner_iters, "outer": info.outer_iters,
-                            "true_resid": info.true_resid, "status": rc, "sap_storage": "f16 links, C_inv, vectors"}
-    # the same batched solve with float32 vectors in the SAP
-    x.zero_()
-    B.qcd_solve(lat.ctx, x, b, 12, _params("half_gauge"))
-    t_h, (rc_h, info_h) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 12, _params("half_gauge")), 1)
-    out["batched_mixed_f32_vectors"] = {"s": t_h, "inner": info_h.inner_iters, "outer": info_h.outer_iters,
-                                        "true_resid": info_h.true_resid, "status": rc_h}
-    # 12 sequential plain float32 solves of the same sources
+                            "true_resid": info.true_resid, "true_resid_per_rhs": res, "status": rc,
+                            "sap_storage": "f16 links, C_inv, vectors"}
+    if f32_vectors:
+        x.zero_()
+        B.qcd_solve(lat.ctx, x, b, 12, _params("half_gauge"))
+        t_h, (rc_h, info_h) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 12, _params("half_gauge")), reps)
+        out["batched_mixed_f32_vectors"] = {"s": t_h, "inner": info_h.inner_iters, "outer": info_h.outer_iters,
+                                            "true_resid": info_h.true_resid, "status": rc_h}
     b1 = [b[i].contiguous() for i in range(12)]
-    x1 = torch.zeros_like(b1[0])
-    B.qcd_solve(lat.ctx, x1, b1[0], 1, _params("single", graph=2))
-    t0 = time.perf_counter()
-    worst = 0.0
-    iters = 0
-    for i in range(12):
-        rc, info = B.qcd_solve(lat.ctx, x1, b1[i], 1, _params("single", graph=2))
-        worst = max(worst, info.true_resid)
-        iters += info.inner_iters
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    out["sequential_plain_f32"] = {"s": t_seq, "inner_total": iters, "true_resid": worst}
-    out["speedup"] = t_seq / t_batch
-    out["speedup_f32_vectors"] = t_seq / t_h
+    x1 = [torch.zeros_like(b1[0]) for _ in range(12)]
+    for name, prec in (("sequential_mixed", "half"), ("sequential_plain_f32", "single")):
+        B.qcd_solve(lat.ctx, x1[0], b1[0], 1, _params(prec))    # warm
+        per = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(12):
+            rc_i, inf = B.qcd_solve(lat.ctx, x1[i], b1[i], 1, _params(prec))
+            per.append({"inner": inf.inner_iters, "outer": inf.outer_iters, "true_resid": inf.true_resid,
+                        "status": rc_i})
+        torch.cuda.synchronize()
+        out[name] = {"s": time.perf_counter() - t0, "inner_total": sum(q["inner"] for q in per),
+                     "true_resid": max(q["true_resid"] for q in per), "per_rhs": per}
+    out["speedup_vs_plain_f32"] = out["sequential_plain_f32"]["s"] / t_batch
+    out["batching_gain"] = out["sequential_mixed"]["s"] / t_batch
+    out["precision_gain"] = out["sequential_plain_f32"]["s"] / out["sequential_mixed"]["s"]
+    out["faster_than_plain_f32"] = bool(t_batch < out["sequential_plain_f32"]["s"])
+    out["setup_s"] = t_setup
     out["clocks"] = clk.stop()
+    lat.close()
+    return out
+
+
+def c3(args):
+    out = north_star_48x4(reps=1, f32_vectors=True)
     return {"config": {"workload": "48^4, eps 0.25, kappa 0.125, c_sw 1.1, 12 spin-colour point sources at the "
                                    "origin; batched float16-storage SAP + float32 BiCGStab + float64 "
-                                   "correction to 1e-10 (device-side graph loop) vs 12 sequential plain float32 "
-                                   "solves (also with the graph loop)"},
+                                   "correction to 1e-10 (device-side graph loop) vs 12 sequential mixed and "
+                                   "12 sequential plain float32 solves (also with the graph loop)"},
             "metric": "time to FP64 residual 1e-10 for 12 right-hand sides", "unit": "s", "results": out}
 
 
@@ -187,7 +230,7 @@ def c5(args):
     dims = (64, 64, 64, 64)
     lat = _lat(dims, 0.2, 0.126, 1.1, 1501)
     b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2501))).cuda().contiguous()
-    clk = ClockSampler("0")
+    clk = ClockSampler(_smi_index())
     clk.start()
     d = _dslash_gbs(lat, b)
     x = torch.zeros_like(b)

@@ -75,6 +75,12 @@ def test_reference_arm_line_contract():
     assert line["higher_is_better"] is True and line["steps"] == 1
     cpu = line["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
+    # a timed complete solve, converted to the benchmark's unit and marked so
+    assert line["extrapolated"] is True and cpu["extrapolated"] is True
+    m = cpu["measured"]
+    assert m["all_converged"] and m["true_resid"] < 1e-10 and m["solves"] == 1
+    # the per-step time is the measured one and fits inside the run
+    assert line["ms_per_step"] * line["steps"] <= 1000.0 * line["wall_s"]
     assert line["e2e"] == {"value": line["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
