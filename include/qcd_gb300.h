@@ -328,14 +328,25 @@ int qcd_profile_enable(qcd_ctx* ctx, int enable);
 int qcd_profile_read(qcd_ctx* ctx, int kernel_class, long long* launches, double* ms, int reset);
 
 /* Launch-shape autotuning (on by default).  With tuning on, the first call of
- * a tunable kernel (the float32 D / D^dag / A operator) for a given number
- * of right-hand sides times each compiled launch shape (threads per block,
- * blocks per SM) on the real arguments and keeps the fastest; the shapes
- * change scheduling only, not the arithmetic.  enable = 0 turns tuning off
- * and forgets the choices (the default shape is then used). */
+ * a tunable kernel for a given key times each compiled shape on the real
+ * arguments and keeps the fastest; the shapes change scheduling only, not
+ * the arithmetic.  Tunable: the float32 D / D^dag / A operator (threads per
+ * block, blocks per SM; key: right-hand sides) and the SAP block kernel of
+ * 4^4 domains (sites per thread; key: SAP storage, lattice, right-hand
+ * sides, n_sap, n_jac -- the whole M_SAP of Algorithm 1 is timed in each
+ * shape).  A solve tunes before it captures its inner loop in a graph.
+ * enable = 0 turns tuning off and forgets the choices (the default shape is
+ * then used). */
 int qcd_set_tuning(qcd_ctx* ctx, int enable);
 
-/* Text report of the tuned choices, one line per key: "<key> <shape> <ms>". */
+/* Fix the SAP block kernel's shape for 4^4 domains: -1 autotuned (default),
+ * 0 one site per thread (256 threads per domain), 1 two sites per thread
+ * (128 threads per domain, each thread two independent site streams).
+ * Every shape computes the same M_SAP bit for bit.  QCD_ERR_ARG otherwise. */
+int qcd_set_sap_shape(qcd_ctx* ctx, int shape);
+
+/* Text report of the tuned choices, one line per key:
+ * "<key> <shape> <ms>", followed by the time of every shape tried. */
 int qcd_tuning_report(qcd_ctx* ctx, char* buf, size_t len);
 
 /* Number of kernels the library has launched on this context so far. */

@@ -83,6 +83,7 @@ _SIGS = {
     "qcd_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), _I]),
     "qcd_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "qcd_set_tuning": (_I, [_P, _I]),
+    "qcd_set_sap_shape": (_I, [_P, _I]),
     "qcd_batch_create": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "qcd_batch_destroy": (_I, [_P]),
     "qcd_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -290,6 +291,12 @@ def qcd_launch_count(ctx):
 
 def qcd_set_tuning(ctx, enable=True):
     return check(ctx, lib().qcd_set_tuning(ctx, int(bool(enable))))
+
+
+def qcd_set_sap_shape(ctx, shape):
+    """SAP block-kernel shape for 4^4 domains: -1 autotuned, 0 one site per
+    thread, 1 two sites per thread."""
+    return check(ctx, lib().qcd_set_sap_shape(ctx, int(shape)))
 
 
 def qcd_measure_fp32_peak(ctx, stream=None):

@@ -668,6 +668,7 @@ struct qcd_ctx {
   void* st_clov16 = nullptr;
   void* st_clov32 = nullptr;
   bool force_generic_sap = false;  // testing: use the generic SAP kernel
+  int sap_shape = -1;              // SAP block-kernel shape: -1 autotuned, 0 one site, 1 two sites per thread
   int inject = 0;                  // testing: QCD_INJECT_* fault (host-side, bounded)
   qcd::Workspace* ws = nullptr;
   qcd::Profiler* prof = nullptr;

@@ -28,21 +28,25 @@
 //   staging layouts per domain (global = shared):
 //     links  f16: __half2 [mu 4][site 256][10]    40 B per link (9 + pad), 8-byte reads
 //            f32: float2  [mu 4][site 256][9]     72 B per link, 8-byte reads
-//     C_inv  f16: uint4   [site 256][11]          two blocks of 40 halves + pad
+//     C_inv  f16: uint4   [site 256][9]           two blocks of 36 halves
 //            f32: float4  [site 256][19]          two blocks of 36 floats + pad
 //   (these site strides make each warp's reads free of shared-memory bank
 //   conflicts)
 //
-// Shared memory: f16 111 KB (two CTAs per SM), f32 176 KB (one CTA per SM).
-// Two mbarriers: the staging copies (once) and the halo copy (once per
-// right-hand side, parity r & 1).
+// Shared memory: f16 103 KB (two CTAs per SM), f32 176 KB (one CTA per SM).
+// Three mbarriers: the staged links and the staged C_inv (once each; the
+// surface term needs only the links, so it starts before C_inv has landed)
+// and the halo copy (once per right-hand side, parity r & 1).
+
+#include <cstdio>
+#include <type_traits>
 
 #include "qcd_internal.cuh"
 
 namespace qcd {
 
 constexpr int ST_THREADS = 256;
-constexpr int C16_U4 = 11;   // uint4 per site, f16 C_inv
+constexpr int C16_U4 = 9;    // uint4 per site, f16 C_inv
 constexpr int L16_H2 = 10;   // half2 per link, f16 links (9 + 1 pad)
 constexpr int C32_F4 = 19;   // float4 per site, f32 C_inv
 
@@ -52,7 +56,7 @@ struct StageT;
 template <>
 struct StageT<true> {
   static constexpr int LINK_BYTES = 4 * 256 * L16_H2 * 4;  // 40960
-  static constexpr int CLOV_BYTES = 256 * C16_U4 * 16;     // 45056
+  static constexpr int CLOV_BYTES = 256 * C16_U4 * 16;     // 36864
   using SIO = F16Spinor;
   // a link is 9 half2 padded to 10 (40 bytes): five 8-byte reads, and the
   // 10-word site stride keeps a half warp's 8-byte reads on distinct banks
@@ -71,13 +75,25 @@ struct StageT<true> {
     }
     return u;
   }
+  // the two blocks are 36 halves each, back to back in 9 uint4 (144 bytes,
+  // an odd number of 16-byte units per site: a quarter warp's 16-byte reads
+  // fall on distinct bank groups); block 0 is uint4 0-3 and the first 8
+  // bytes of uint4 4, block 1 the last 8 bytes of uint4 4 and uint4 5-8
   __device__ static void clover_block(const unsigned char* base, int site, int b, CloverBlockF32& blk) {
     const uint4* p = reinterpret_cast<const uint4*>(base) + site * C16_U4;
-    // block b occupies halves [40 b, 40 b + 36)
-    const __half2* h = reinterpret_cast<const __half2*>(p) + 20 * b;
+    unsigned w[18];
+    const uint2 mid = reinterpret_cast<const uint2*>(p + 4)[b];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 v = p[b == 0 ? k : 5 + k];
+      const int o = b == 0 ? 4 * k : 2 + 4 * k;
+      w[o] = v.x; w[o + 1] = v.y; w[o + 2] = v.z; w[o + 3] = v.w;
+    }
+    w[b == 0 ? 16 : 0] = mid.x;
+    w[b == 0 ? 17 : 1] = mid.y;
 #pragma unroll
     for (int k = 0; k < 18; ++k) {
-      const float2 v = __half22float2(h[k]);
+      const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
       blk.r[2 * k] = v.x;
       blk.r[2 * k + 1] = v.y;
     }
@@ -452,30 +468,48 @@ __device__ __forceinline__ void st_store_x(float4* sx, int s, const Spinor<float
   }
 }
 
-// HALF: float16 links and C_inv (two CTAs per SM); SIO: storage of s and x
-template <bool HALF, typename SIO>
-__global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF, SIO> a) {
+// Record a wait that gave up and leave: give the copies one more bounded
+// wait each (the decision is uniform across the CTA).
+__device__ __forceinline__ void st_give_up(int* status, int tid, bool wait0, uint64_t* bar0, unsigned par0,
+                                           bool wait1, uint64_t* bar1, unsigned par1) {
+  if (tid == 0) atomicExch(status, QCD_ERR_TIMEOUT);
+  if (wait0) mbar_wait_bounded(bar0, par0);
+  if (wait1) mbar_wait_bounded(bar1, par1);
+}
+
+// HALF: float16 links and C_inv (two CTAs per SM); SIO: storage of s and x.
+// SPT: sites per thread.  With SPT = 1 a CTA has 256 threads, one per site;
+// with SPT = 2 it has 128 threads, thread tau holding sites tau and
+// tau + 128 (the same x, y, z, t and t + 2), which gives each thread two
+// independent streams of the same arithmetic.  The arithmetic per site is
+// the same in both; the autotuner picks the faster shape.
+template <bool HALF, typename SIO, int SPT>
+__global__ void __launch_bounds__(ST_THREADS / SPT, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF, SIO> a) {
+  constexpr int NT = ST_THREADS / SPT;
   extern __shared__ __align__(128) unsigned char smem[];
   using ST = StageT<HALF>;
   float4* sx = reinterpret_cast<float4*>(smem);                              // 24 KB
   unsigned char* sl = smem + SX_BYTES;                                        // links
   unsigned char* sc = sl + ST::LINK_BYTES;                                     // C_inv
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);  // staging copies
-  uint64_t* hbar = bar + 1;                                              // halo copy
+  uint64_t* lbar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);  // staged links
+  uint64_t* cbar = lbar + 1;                                          // staged C_inv
+  uint64_t* hbar = lbar + 2;                                          // halo copy
   const Geom& g = a.g;
   if (loop_idle(g)) return;
-  const int s = threadIdx.x;
+  const int tid = threadIdx.x;
   const int dom = a.colour * g.nhalf + blockIdx.x;
 
   // programmatic dependent launch: the next launch in the stream may start
   // its CTAs while this grid drains
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if (s == 0) {
-    mbar_init(bar, 1);
+  if (tid == 0) {
+    mbar_init(lbar, 1);
+    mbar_init(cbar, 1);
     mbar_init(hbar, 1);
-    mbar_expect_tx(bar, ST::LINK_BYTES + ST::CLOV_BYTES + a.extra_tx);
-    bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, bar);
-    bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, bar);
+    mbar_expect_tx(lbar, ST::LINK_BYTES + a.extra_tx);
+    bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, lbar);
+    mbar_expect_tx(cbar, ST::CLOV_BYTES);
+    bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, cbar);
   }
   // the staged links and C_inv are constant during a solve; everything read
   // below may come from the previous launch, which must be complete
@@ -484,89 +518,126 @@ __global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_staged_kernel(St
     const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
     const int rhs_off = r * g.ndom;
     if (r > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
-    if (a.do_surface && s == 0) {
+    if (a.do_surface && tid == 0) {
       // the halo lands in the slots (the start of the x buffer); order the
       // earlier generic accesses to it before the asynchronous copy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(hbar, HALO_BYTES + a.extra_htx);
       bulk_copy_g2s(sx, a.halo + (size_t)domr * HALO_F4, HALO_BYTES, hbar);
     }
-    Spinor<float> src;
-    if (a.s_in32.p) a.s_in32.load(g, domr, s, src);
-    else a.s_in.load(g, domr, s, src);
+    Spinor<float> src[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+      if (a.s_in32.p) a.s_in32.load(g, domr, tid + j * NT, src[j]);
+      else a.s_in.load(g, domr, tid + j * NT, src[j]);
+    }
     if (r == 0) __syncthreads();  // barrier initialisation visible to every thread
     {
-      const bool ok_st = r > 0 || mbar_wait_bounded(bar, 0);
+      const bool ok_l = r > 0 || mbar_wait_bounded(lbar, 0);
       const bool ok_h = !a.do_surface || mbar_wait_bounded(hbar, r & 1);
-      if (__syncthreads_or(!(ok_st && ok_h))) {
-        // a wait gave up: record it, give the copies one more bounded wait and
-        // leave (the decision is uniform across the CTA)
-        if (s == 0) atomicExch(a.status, QCD_ERR_TIMEOUT);
-        if (!ok_st) mbar_wait_bounded(bar, 0);
-        if (!ok_h) mbar_wait_bounded(hbar, r & 1);
+      if (__syncthreads_or(!(ok_l && ok_h))) {
+        st_give_up(a.status, tid, !ok_l, lbar, 0, !ok_h, hbar, r & 1);
+        if (r == 0) mbar_wait_bounded(cbar, 0);
         return;
       }
     }
-    Spinor<float> acc;
+    Spinor<float> acc[SPT];
     if (a.do_surface) {
-      st_face_tasks<HALF>(g, sl, dom, s, sx);
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) st_face_tasks<HALF>(g, sl, dom, tid + j * NT, sx);
       __syncthreads();
-      zero(acc);
-      st_face_sum(sx, s, acc);
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        zero(acc[j]);
+        st_face_sum(sx, tid + j * NT, acc[j]);
+      }
       __syncthreads();  // every thread has taken its face slots before x overwrites them
-      st_clover<HALF>(sc, s, acc);
-#pragma unroll
-      for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          src.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
-          src.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
-        }
     }
-    if (s < 48) sx[(s >> 3) * SX_STRIDE + SX_GHOST + (s & 7)] = make_float4(0.f, 0.f, 0.f, 0.f);  // face slots overlap it
-    st_store_x(sx, s, src);
+    if (r == 0) {
+      // C_inv is first needed here
+      const bool ok_c = mbar_wait_bounded(cbar, 0);
+      if (__syncthreads_or(!ok_c)) {
+        st_give_up(a.status, tid, true, cbar, 0, false, cbar, 0);
+        return;
+      }
+    }
+    if (a.do_surface) {
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        st_clover<HALF>(sc, tid + j * NT, acc[j]);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            src[j].v[sp][c].re = fmaf(a.kappa, acc[j].v[sp][c].re, src[j].v[sp][c].re);
+            src[j].v[sp][c].im = fmaf(a.kappa, acc[j].v[sp][c].im, src[j].v[sp][c].im);
+          }
+      }
+    }
+    if (tid < 48) sx[(tid >> 3) * SX_STRIDE + SX_GHOST + (tid & 7)] = make_float4(0.f, 0.f, 0.f, 0.f);  // face slots overlap it
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) st_store_x(sx, tid + j * NT, src[j]);
     __syncthreads();
 
-    Spinor<float> xk = src;
+    Spinor<float> xk[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) xk[j] = src[j];
     const int napp = a.n_jac + (a.do_update ? 1 : 0);
     for (int it = 0; it < napp; ++it) {
       // the x hops start the sum (no zeroing); the t hops' warp-uniform
       // branches follow, then one straight-line stretch (y, z hops and the
       // clover multiply)
-      st_intra<0, HALF, true>(sx, sl, s, acc);
-      st_intra<3, HALF>(sx, sl, s, acc);
-      st_intra<1, HALF>(sx, sl, s, acc);
-      st_intra<2, HALF>(sx, sl, s, acc);
-      st_clover<HALF>(sc, s, acc);
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) {
+        const int s = tid + j * NT;
+        st_intra<0, HALF, true>(sx, sl, s, acc[j]);
+        st_intra<3, HALF>(sx, sl, s, acc[j]);
+        st_intra<1, HALF>(sx, sl, s, acc[j]);
+        st_intra<2, HALF>(sx, sl, s, acc[j]);
+        st_clover<HALF>(sc, s, acc[j]);
+      }
       if (it < a.n_jac) {
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp)
+        for (int j = 0; j < SPT; ++j)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            xk.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, src.v[sp][c].re);
-            xk.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, src.v[sp][c].im);
-          }
+          for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              xk[j].v[sp][c].re = fmaf(a.kappa, acc[j].v[sp][c].re, src[j].v[sp][c].re);
+              xk[j].v[sp][c].im = fmaf(a.kappa, acc[j].v[sp][c].im, src[j].v[sp][c].im);
+            }
         __syncthreads();
-        st_store_x(sx, s, xk);
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) st_store_x(sx, tid + j * NT, xk[j]);
         __syncthreads();
       } else {
-        Spinor<float> b;
-        a.b.load(g, domr, s, b);
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp)
+        for (int j = 0; j < SPT; ++j) {
+          const int s = tid + j * NT;
+          Spinor<float> b;
+          a.b.load(g, domr, s, b);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float re = src.v[sp][c].re + b.v[sp][c].re - xk.v[sp][c].re;
-            const float im = src.v[sp][c].im + b.v[sp][c].im - xk.v[sp][c].im;
-            acc.v[sp][c].re = fmaf(a.kappa, acc.v[sp][c].re, re);
-            acc.v[sp][c].im = fmaf(a.kappa, acc.v[sp][c].im, im);
-          }
-        a.s_out.store(g, domr, s, acc);
+          for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float re = src[j].v[sp][c].re + b.v[sp][c].re - xk[j].v[sp][c].re;
+              const float im = src[j].v[sp][c].im + b.v[sp][c].im - xk[j].v[sp][c].im;
+              acc[j].v[sp][c].re = fmaf(a.kappa, acc[j].v[sp][c].re, re);
+              acc[j].v[sp][c].im = fmaf(a.kappa, acc[j].v[sp][c].im, im);
+            }
+          a.s_out.store(g, domr, s, acc[j]);
+        }
       }
     }
-    if (a.do_halo) st_halo_out<HALF>(g, sx, sl, a.halo, dom, rhs_off, s);  // sx holds the final iterate
-    if (a.x_store) a.x.store(g, domr, s, xk);
-    if (a.x_out32.p) a.x_out32.store(g, domr, s, xk);
+    if (a.do_halo) {  // sx holds the final iterate
+#pragma unroll
+      for (int j = 0; j < SPT; ++j) st_halo_out<HALF>(g, sx, sl, a.halo, dom, rhs_off, tid + j * NT);
+    }
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+      if (a.x_store) a.x.store(g, domr, tid + j * NT, xk[j]);
+      if (a.x_out32.p) a.x_out32.store(g, domr, tid + j * NT, xk[j]);
+    }
   }
 }
 
@@ -598,20 +669,23 @@ __global__ void build_clover_stage_kernel(Geom g, const double2* c64, uint4* c16
   for (int b = 0; b < 2; ++b) {
     for (int k = 0; k < 18; ++k) {
       const double2 v = c64[(((size_t)(dom * 36 + 18 * b + k)) << 8) + s];
-      h[20 * b + k] = __floats2half2_rn((float)v.x, (float)v.y);
+      h[18 * b + k] = __floats2half2_rn((float)v.x, (float)v.y);
       f[36 * b + 2 * k] = (float)v.x;
       f[36 * b + 2 * k + 1] = (float)v.y;
     }
-    h[20 * b + 18] = __floats2half2_rn(0.f, 0.f);
-    h[20 * b + 19] = __floats2half2_rn(0.f, 0.f);
   }
-  for (int k = 40; k < 44; ++k) h[k] = __floats2half2_rn(0.f, 0.f);
   for (int k = 72; k < 76; ++k) f[k] = 0.f;
 }
 
 bool sap_staged_available(const qcd_ctx* ctx) {
   const Geom& g = ctx->geom;
   return g.d[0] == 4 && g.d[1] == 4 && g.d[2] == 4 && g.d[3] == 4 && ctx->st_link16 && ctx->st_clov16;
+}
+
+// x buffer, staged links and C_inv, three mbarriers
+template <bool HALF>
+constexpr int st_smem_bytes() {
+  return SX_BYTES + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 32;
 }
 
 void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
@@ -623,13 +697,19 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_link32, nd * StageT<false>::LINK_BYTES));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov16, nd * StageT<true>::CLOV_BYTES));
     QCD_CUDA_CHECK(cudaMalloc(&ctx->st_clov32, nd * StageT<false>::CLOV_BYTES));
-    const int s16 = SX_BYTES + StageT<true>::LINK_BYTES + StageT<true>::CLOV_BYTES + 16;
-    const int s32 = SX_BYTES + StageT<false>::LINK_BYTES + StageT<false>::CLOV_BYTES + 16;
-    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F16Spinor>,
+    const int s16 = st_smem_bytes<true>();
+    const int s32 = st_smem_bytes<false>();
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F16Spinor, 1>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
-    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F32Spinor>,
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F16Spinor, 2>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
-    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<false, F32Spinor>,
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F32Spinor, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<true, F32Spinor, 2>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<false, F32Spinor, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<false, F32Spinor, 2>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
   }
   LaunchScope ls(ctx, QCD_KC_OTHER, st);
@@ -643,9 +723,9 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
 // Algorithm 1 as 2 (n_sap + 1) launches.  s_first_in32 (float32) is the
 // first sweep's input, the source itself.  The final iterate goes to x_out32
 // if it is set, else to x.  halo holds 96 bytes per site and right-hand side.
-template <bool HALF, typename SIO>
-static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b, F32Spinor x_out32,
-                            float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+template <bool HALF, typename SIO, int SPT>
+static void staged_sequence_shape(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b,
+                                  F32Spinor x_out32, float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
   StagedArgs<HALF, SIO> a;
   a.g = ctx->geom;
   a.nrhs = nrhs;
@@ -663,7 +743,6 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
   // wait gives up and reports QCD_ERR_TIMEOUT
   a.extra_tx = ctx->inject == QCD_INJECT_STAGING_WAIT ? 16 : 0;
   a.extra_htx = ctx->inject == QCD_INJECT_HALO_WAIT ? 16 : 0;
-  const int smem = SX_BYTES + StageT<HALF>::LINK_BYTES + StageT<HALF>::CLOV_BYTES + 16;
   for (int sweep = 0; sweep <= n_sap; ++sweep) {
     a.s_in32 = sweep == 0 ? s_first_in32 : F32Spinor{nullptr};
     a.do_update = sweep == n_sap ? 0 : 1;
@@ -677,18 +756,46 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
       LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(ctx->geom.nhalf);
-      cfg.blockDim = dim3(ST_THREADS);
-      cfg.dynamicSmemBytes = smem;
+      cfg.blockDim = dim3(ST_THREADS / SPT);
+      cfg.dynamicSmemBytes = st_smem_bytes<HALF>();
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
       attr[0].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      QCD_CUDA_CHECK(cudaLaunchKernelEx(&cfg, sap_staged_kernel<HALF, SIO>, a));
+      QCD_CUDA_CHECK(cudaLaunchKernelEx(&cfg, sap_staged_kernel<HALF, SIO, SPT>, a));
       check_launch();
     }
   }
+}
+
+// The block-kernel shape (sites per thread) is chosen by the autotuner on
+// the first M_SAP of each precision, lattice, right-hand-side count and
+// n_jac: it times the whole sequence in every shape on the caller's
+// buffers (M_SAP is a function of its input alone, so the repeated runs
+// leave the same result) and keeps the faster.  qcd_set_sap_shape fixes it.
+static const char* const kSapShapes[] = {"256x1site", "128x2sites"};
+
+template <bool HALF, typename SIO>
+static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b, F32Spinor x_out32,
+                            float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+  auto run = [&](int v) {
+    if (v == 1)
+      staged_sequence_shape<HALF, SIO, 2>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st);
+    else
+      staged_sequence_shape<HALF, SIO, 1>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st);
+  };
+  int v = ctx->sap_shape;
+  if (v < 0) {
+    const Geom& g = ctx->geom;
+    char key[128];
+    std::snprintf(key, sizeof key, "sap_staged_%s L%dx%dx%dx%d nrhs%d n_sap%d n_jac%d",
+                  HALF ? (std::is_same<SIO, F16Spinor>::value ? "f16" : "f16gauge") : "f32", g.L[0], g.L[1], g.L[2],
+                  g.L[3], nrhs, n_sap, n_jac);
+    v = tune_pick(ctx, key, 2, kSapShapes, run, st);
+  }
+  run(v);
 }
 
 void sap_staged_sequence_f32(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b,

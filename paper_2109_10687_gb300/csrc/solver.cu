@@ -717,8 +717,10 @@ static int bicgstab_sap(qcd_ctx* ctx, Workspace* w, const float4* b32, int nrhs,
                    G.mode != mode || G.kappa != ctx->kappa)) {
     G.reset();
     // the autotuner cannot time launch shapes inside a capture: run the
-    // operator kernel of the loop once beforehand (scratch buffers only)
+    // operator and SAP kernels of the loop once beforehand (into scratch
+    // buffers the loop overwrites before reading; p holds the source here)
     dslash_launch(ctx, w->t, w->zp, QCD_PREC_SINGLE, MODE_A, nrhs, st);
+    sap_apply_launch(ctx, w->zr, w->p, nrhs, P.n_sap, P.n_jac, P.sap_prec, w->sap_s, w->sap_x16, w->sap_b16, st);
     cudaGraph_t gr;
     const long long c_start = ctx->launches;
     long long c0 = c_start;

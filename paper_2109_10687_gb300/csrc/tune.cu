@@ -19,6 +19,7 @@ struct Tuner {
     int variant;
     float ms;
     std::string name;
+    std::string all;  // every shape tried: "name ms, ..."
   };
   std::map<std::string, Entry> best;
 };
@@ -46,6 +47,7 @@ int tune_pick(qcd_ctx* ctx, const char* key, int nvariants, const char* const* n
   QCD_CUDA_CHECK(cudaEventCreate(&b));
   int best_v = 0;
   float best_ms = 1e30f;
+  std::string all;
   for (int v = 0; v < nvariants; ++v) {
     run(v);  // warm-up
     QCD_CUDA_CHECK(cudaEventRecord(a, st));
@@ -55,6 +57,9 @@ int tune_pick(qcd_ctx* ctx, const char* key, int nvariants, const char* const* n
     float ms = 0.f;
     QCD_CUDA_CHECK(cudaEventElapsedTime(&ms, a, b));
     ms /= 3.f;
+    char item[96];
+    std::snprintf(item, sizeof item, "%s%s %.4f", v ? ", " : "", names ? names[v] : std::to_string(v).c_str(), ms);
+    all += item;
     if (ms < best_ms) {
       best_ms = ms;
       best_v = v;
@@ -63,7 +68,7 @@ int tune_pick(qcd_ctx* ctx, const char* key, int nvariants, const char* const* n
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   ctx->launches += 4LL * nvariants;
-  t->best[key] = {best_v, best_ms, names ? names[best_v] : std::to_string(best_v)};
+  t->best[key] = {best_v, best_ms, names ? names[best_v] : std::to_string(best_v), all};
   return best_v;
 }
 
@@ -78,13 +83,20 @@ extern "C" int qcd_set_tuning(qcd_ctx* ctx, int enable) {
   return QCD_OK;
 }
 
+extern "C" int qcd_set_sap_shape(qcd_ctx* ctx, int shape) {
+  if (!ctx || shape < -1 || shape > 1) return QCD_ERR_ARG;
+  ctx->sap_shape = shape;
+  return QCD_OK;
+}
+
 extern "C" int qcd_tuning_report(qcd_ctx* ctx, char* buf, size_t len) {
   if (!ctx || !buf || len == 0) return QCD_ERR_ARG;
   std::string out;
   for (auto& kv : tuner_of(ctx)->best) {
     char line[256];
-    std::snprintf(line, sizeof line, "%s %s %.4f ms\n", kv.first.c_str(), kv.second.name.c_str(), kv.second.ms);
+    std::snprintf(line, sizeof line, "%s %s %.4f ms", kv.first.c_str(), kv.second.name.c_str(), kv.second.ms);
     out += line;
+    out += " [" + kv.second.all + "]\n";
   }
   std::snprintf(buf, len, "%s", out.c_str());
   return QCD_OK;
