@@ -277,15 +277,44 @@ def c5ragged(args):
     total = sum(vols)
     gbs = D_BYTES_PER_SITE * total / (ms * 1e-3) / 1e9
     xs = [torch.zeros_like(b) for b in bs]
-    B.qcd_batch_solve(bt, xs, bs, _params("half_gauge"))
-    t, (rc, infos) = _timed(lambda: B.qcd_batch_solve(bt, xs, bs, _params("half_gauge")), 1)
+    solves = {}
+    reps = max(3, args.steps)
+    for prec in ("half", "half_gauge"):
+        # shared launches: every SAP half-sweep, operator and BLAS-1 step of an
+        # iteration one launch over the 32 lattices, the inner loop one graph
+        B.qcd_batch_set_shared(bt, True)
+        B.qcd_batch_solve(bt, xs, bs, _params(prec))
+        n0 = B.qcd_launch_count(lats[0].ctx)
+        t, (rc, infos) = _timed(lambda: B.qcd_batch_solve(bt, xs, bs, _params(prec)), reps)
+        launches = (B.qcd_launch_count(lats[0].ctx) - n0) / reps
+        # the same batch as 32 concurrent solves (one host thread and stream each)
+        B.qcd_batch_set_shared(bt, False)
+        B.qcd_batch_solve(bt, xs, bs, _params(prec))
+        tc, (rcc, infosc) = _timed(lambda: B.qcd_batch_solve(bt, xs, bs, _params(prec)), reps)
+        B.qcd_batch_set_shared(bt, True)
+        # and as 32 solves one after the other
+        ones = [torch.zeros_like(b) for b in bs]
+        for lat, x1, b1 in zip(lats, ones, bs):
+            B.qcd_solve(lat.ctx, x1, b1, 1, _params(prec))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for lat, x1, b1 in zip(lats, ones, bs):
+                B.qcd_solve(lat.ctx, x1, b1, 1, _params(prec))
+        torch.cuda.synchronize()
+        ts = (time.perf_counter() - t0) / reps
+        solves[prec] = {
+            "shared_launches_s": t, "status": rc, "worst_true_resid": max(i.true_resid for i in infos),
+            "inner_per_lattice": [i.inner_iters for i in infos], "outer_per_lattice": [i.outer_iters for i in infos],
+            "launches_per_batch_solve": launches,
+            "concurrent_threads_s": tc, "concurrent_worst_true_resid": max(i.true_resid for i in infosc),
+            "sequential_s": ts, "speedup_vs_sequential": ts / t, "speedup_vs_concurrent": tc / t}
     B.qcd_batch_destroy(bt)
     return {"config": {"workload": "ragged batch of 32 lattices, extents from {8, 16} per direction, eps 0.3, "
                                    "kappa ~ U[0.115, 0.125], c_sw 1.0, seeds 5000 + i", "sites": total},
             "metric": "batched Dslash GB/s (one launch); batched solve time to 1e-10", "unit": "GB/s; s",
             "results": {"dslash_batched": {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak, "peak_kind": kind},
-                        "batched_solve_s": t, "status": rc, "worst_true_resid": max(i.true_resid for i in infos),
-                        "inner_max": max(i.inner_iters for i in infos)}}
+                        "batched_solve": solves}}
 
 
 # Per-site flop of one SAP-BiCGStab iteration in the paper's accounting

@@ -284,13 +284,29 @@ const char* qcd_batch_last_error(const qcd_batch* batch);
 int qcd_batch_apply_D(qcd_batch* batch, void* const* out, const void* const* in, int dagger, void* stream);
 
 /* Solve D_i x_i = b_i for every lattice (one right-hand side each, canonical
- * float64 fields as in qcd_solve).  The lattices' solves run at the same
- * time on one stream each (ordered after `stream`), so their kernels
- * interleave on the GPU.  infos (may be NULL) receives one record per
- * lattice; returns the first failing lattice's status, QCD_OK if all met
- * params->tol. */
+ * float64 fields as in qcd_solve; Algorithm 4 around Algorithm 5 on
+ * A M_SAP, Sec. 3).  When every lattice has 4^4 domains, outer_restart = 0
+ * and residual_prec = 1, the lattices are solved in SHARED LAUNCHES: each
+ * SAP half-sweep (Algorithm 1), each application of A and of the float64 D,
+ * and each fused BLAS-1 step of Algorithm 5 is one kernel launch over every
+ * lattice, through work lists built on the first call; the inner loop is one
+ * CUDA graph with a conditional while node (use_graph = 2; otherwise the
+ * kernels are launched one by one), run while any lattice iterates.  A
+ * lattice that has converged stops there while the others continue; per
+ * lattice the iterations and the float64 true residual are those of its own
+ * Algorithm 4/5.  The batch allocates its buffers on the first call (about
+ * 1.5 KB per site over all lattices) and keeps them.  Other batches (or
+ * after qcd_batch_set_shared(batch, 0)) run the lattices' solves at the same
+ * time on one stream each, so that their kernels interleave.  Both forms
+ * are ordered after `stream`.  infos (may be NULL) receives one record per
+ * lattice (seconds: the whole batch); returns the first failing lattice's
+ * status, QCD_OK if all met params->tol. */
 int qcd_batch_solve(qcd_batch* batch, double* const* x, const double* const* b, int on_device,
                     const qcd_solve_params* params, qcd_solve_info* infos, void* stream);
+
+/* 1 (default): qcd_batch_solve uses shared launches where it can; 0: always
+ * the concurrent per-lattice solves. */
+int qcd_batch_set_shared(qcd_batch* batch, int enable);
 
 /* ---- gradients -------------------------------------------------------- */
 

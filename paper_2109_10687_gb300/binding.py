@@ -90,6 +90,7 @@ _SIGS = {
     "qcd_batch_apply_D": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
     "qcd_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.POINTER(SolveParams),
                              ctypes.POINTER(SolveInfo), _P]),
+    "qcd_batch_set_shared": (_I, [_P, _I]),
     "qcd_tuning_report": (_I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "qcd_measure_fp32_peak": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P]),
     "qcd_device_status": (_I, [_P, ctypes.POINTER(_I), _I, _P]),
@@ -351,6 +352,11 @@ def qcd_batch_apply_D(batch, outs, ins, dagger=0, stream=None):
     o = (ctypes.c_void_p * len(outs))(*[_ptr(t) for t in outs])
     i = (ctypes.c_void_p * len(ins))(*[_ptr(t) for t in ins])
     return _batch_check(batch, lib().qcd_batch_apply_D(batch, o, i, int(dagger), _stream(stream)))
+
+
+def qcd_batch_set_shared(batch, enable=True):
+    """1: qcd_batch_solve in shared launches where supported; 0: concurrent per-lattice solves."""
+    return _batch_check(batch, lib().qcd_batch_set_shared(batch, int(bool(enable))))
 
 
 def qcd_batch_solve(batch, xs, bs, params=None, stream=None, raise_on_error=True):

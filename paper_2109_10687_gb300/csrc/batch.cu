@@ -3,9 +3,13 @@
 //
 // qcd_batch_apply_D applies every lattice's float32 operator in one kernel
 // launch through a work list: each lattice owns a contiguous range of blocks
-// and its descriptor (geometry, field pointers, kappa).  qcd_batch_solve runs
-// the lattices' solves at the same time, one host thread and one stream per
-// lattice, so that the GPU interleaves their kernels.
+// and its descriptor (geometry, field pointers, kappa).  qcd_batch_solve
+// solves every lattice in shared launches (ragged.cu): each SAP half-sweep,
+// operator application and BLAS-1 step of an iteration is one launch over
+// all lattices.  Batches the shared launches do not cover (a lattice without
+// 4^4 domains, the flexible GMRES outer solver, the double-float residual)
+// run the lattices' solves concurrently instead, one host thread and one
+// stream per lattice.
 
 #include <thread>
 #include <vector>
@@ -20,6 +24,8 @@ struct qcd_batch {
   cudaEvent_t desc_free = nullptr;   // the previous descriptor copy has completed
   int* d_block_lat = nullptr;        // lattice of every block of the one-launch D
   long long nblocks = 0;
+  qcd::RaggedWS* rws = nullptr;      // buffers of the shared-launch solve
+  bool shared = true;                // solve in shared launches where supported
   std::string err;
 };
 
@@ -60,7 +66,14 @@ extern "C" int qcd_batch_destroy(qcd_batch* b) {
   if (b->h_desc) cudaFreeHost(b->h_desc);
   if (b->desc_free) cudaEventDestroy(b->desc_free);
   if (b->d_block_lat) cudaFree(b->d_block_lat);
+  qcd::ragged_free(b->rws);
   delete b;
+  return QCD_OK;
+}
+
+extern "C" int qcd_batch_set_shared(qcd_batch* b, int enable) {
+  if (!b) return QCD_ERR_ARG;
+  b->shared = enable != 0;
   return QCD_OK;
 }
 
@@ -120,6 +133,18 @@ extern "C" int qcd_batch_solve(qcd_batch* b, double* const* x, const double* con
   try {
     QCD_REQUIRE(x && rhs, QCD_ERR_ARG, "qcd_batch_solve: null arrays");
     const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i) QCD_REQUIRE(x[i] && rhs[i], QCD_ERR_ARG, "qcd_batch_solve: null field pointer");
+    qcd_solve_params P;
+    if (params) P = *params;
+    else qcd_solve_params_default(&P);
+    QCD_REQUIRE(P.tol > 0 && P.inner_tol > 0 && P.max_outer >= 1 && P.max_inner >= 1 && P.n_sap >= 0 && P.n_jac >= 1,
+                QCD_ERR_ARG, "qcd_batch_solve: bad parameters");
+    QCD_REQUIRE(P.sap_prec == QCD_PREC_SINGLE || P.sap_prec == QCD_PREC_HALF || P.sap_prec == QCD_PREC_HALF_GAUGE,
+                QCD_ERR_ARG, "qcd_batch_solve: sap_prec must be SINGLE, HALF or HALF_GAUGE");
+    if (b->shared && ragged_eligible(b->ctx, P)) {
+      const int rc = ragged_solve(b->ctx, b->rws, x, rhs, on_device, P, infos, (cudaStream_t)stream, b->err);
+      return rc;
+    }
     QCD_CUDA_CHECK(cudaStreamSynchronize((cudaStream_t)stream));  // inputs ready before the lattices start
     std::vector<int> rc(n, QCD_OK);
     std::vector<qcd_solve_info> info(n);
@@ -144,5 +169,8 @@ extern "C" int qcd_batch_solve(qcd_batch* b, double* const* x, const double* con
   } catch (const qcd::Error& e) {
     b->err = e.msg;
     return e.code;
+  } catch (...) {
+    b->err = "qcd_batch_solve: unknown error";
+    return QCD_ERR_CUDA;
   }
 }

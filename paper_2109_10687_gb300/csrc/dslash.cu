@@ -239,6 +239,48 @@ void dslash_batch_launch(const BatchDesc* d_desc, const int* d_block_lat, long l
   check_launch();
 }
 
+// Ragged batch solve: the float32 A of A M_SAP for every lattice in one
+// launch (which 0: q = A zp, 1: t = A zr; lattices that have stopped
+// iterating return at once), and the float64 D of Algorithm 4 (which 2:
+// r64 = D x64, every lattice).  Block b belongs to lattice block_lat[b],
+// whose descriptor the block copies to shared memory.
+__device__ __forceinline__ void copy_lat_desc(const LatDesc* __restrict__ desc, int lat, LatDesc& sd) {
+  const int* src = reinterpret_cast<const int*>(desc + lat);
+  int* dst = reinterpret_cast<int*>(&sd);
+  for (int k = threadIdx.x; k < (int)(sizeof(LatDesc) / sizeof(int)); k += blockDim.x) dst[k] = __ldg(src + k);
+}
+__global__ void __launch_bounds__(128, 3) lat_dslash_a_kernel(const LatDesc* __restrict__ desc,
+                                                              const int* __restrict__ block_lat, int which) {
+  __shared__ LatDesc sd;
+  copy_lat_desc(desc, __ldg(block_lat + blockIdx.x), sd);
+  __syncthreads();
+  if (loop_idle(sd.g) || *(volatile const int*)sd.done) return;
+  const long long gid = ((long long)blockIdx.x - sd.block_begin) * 128 + threadIdx.x;
+  if (gid >= sd.g.vol) return;
+  const LinkPtr<float> U{sd.u32};
+  const CloverPtrF32 cinv{sd.cinv32};
+  if (which == 0) dslash_site<float, MODE_A, true>(sd.g, F32Spinor{sd.q}, F32Spinor{sd.zp}, U, cinv, sd.kappa, gid, 0);
+  else dslash_site<float, MODE_A, true>(sd.g, F32Spinor{sd.t}, F32Spinor{sd.zr}, U, cinv, sd.kappa, gid, 0);
+}
+__global__ void __launch_bounds__(128) lat_dslash64_kernel(const LatDesc* __restrict__ desc,
+                                                           const int* __restrict__ block_lat) {
+  __shared__ LatDesc sd;
+  copy_lat_desc(desc, __ldg(block_lat + blockIdx.x), sd);
+  __syncthreads();
+  const long long gid = ((long long)blockIdx.x - sd.block_begin) * 128 + threadIdx.x;
+  if (gid >= sd.g.vol) return;
+  dslash_site<double, MODE_D>(sd.g, F64Spinor{sd.r64}, F64Spinor{sd.x64}, LinkPtr<double>{sd.u64},
+                              CloverPtrF64{sd.clov64}, sd.kappa64, gid, 0);
+}
+
+void lat_dslash_launch(const LatDesc* d_lat, const int* d_block_lat, long long blocks, int which, cudaStream_t st) {
+  static_assert(sizeof(LatDesc) % sizeof(int) == 0, "descriptor is copied as ints");
+  QCD_REQUIRE(blocks < (1LL << 31), QCD_ERR_ARG, "batch too large for one launch");
+  if (which == 2) lat_dslash64_kernel<<<(unsigned)blocks, 128, 0, st>>>(d_lat, d_block_lat);
+  else lat_dslash_a_kernel<<<(unsigned)blocks, 128, 0, st>>>(d_lat, d_block_lat, which);
+  check_launch();
+}
+
 template <typename R>
 __global__ void clover_apply_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in,
                                     typename Prec<R>::CP clov) {

@@ -34,6 +34,7 @@
 #include <cstdint>
 #include <functional>
 #include <string>
+#include <vector>
 #include <utility>
 
 #include "qcd_gb300.h"
@@ -775,6 +776,49 @@ struct BatchDesc {
 };
 void dslash_batch_launch(const BatchDesc* d_desc, const int* d_block_lat, long long total_blocks, int dagger,
                          cudaStream_t st);
+
+// One lattice of a ragged batch solve, as the shared launches see it: its
+// geometry and operator, and where its vectors lie in the batch's ragged
+// buffers (built once per batch).
+struct LatDesc {
+  Geom g;
+  float kappa;
+  double kappa64;
+  const float2* u32;
+  const float4* cinv32;
+  const double2* u64;
+  const double2* clov64;
+  float4 *x, *q, *t, *zp, *zr, *b32;   // float32 internal fields of Algorithm 5
+  double2 *x64, *r64, *b64;            // float64 internal fields of Algorithm 4
+  const int* done;                     // this lattice's BiCGStab stop flag
+  long long block_begin;               // first 128-thread block of this lattice
+};
+// which: 0 q = A zp, 1 t = A zr (float32; lattices whose done flag is set
+// are skipped), 2 r64 = D x64 (float64)
+void lat_dslash_launch(const LatDesc* d_lat, const int* d_block_lat, long long blocks, int which, cudaStream_t st);
+
+// M_SAP (Algorithm 1) of every lattice of a ragged batch in shared launches:
+// one launch per half-sweep covers every lattice's domains of that colour.
+struct SapLat {
+  const qcd_ctx* ctx;
+  F32Spinor in, out;   // source and result (float32 internal layout)
+  float4* s32;         // the s vector in float32 ...
+  uint4* s16;          // ... or in float16 storage (values, per-site norms)
+  float* s16n;
+  float4* halo;        // face halo, 96 bytes per site
+  const int* skip;     // nonzero: the lattice has stopped iterating
+};
+struct SapBatchPlan;
+struct RaggedWS;
+bool ragged_eligible(const std::vector<qcd_ctx*>& ctx, const qcd_solve_params& P);
+int ragged_solve(const std::vector<qcd_ctx*>& ctx, RaggedWS*& ws, double* const* x, const double* const* b,
+                 int on_device, const qcd_solve_params& P, qcd_solve_info* infos, cudaStream_t user_st,
+                 std::string& err);
+void ragged_free(RaggedWS* ws);
+SapBatchPlan* sap_batch_plan(const std::vector<SapLat>& lats, int sap_prec, int n_sap, int n_jac, int* status,
+                             const int* run_flag);
+void sap_batch_run(const SapBatchPlan* plan, qcd_ctx* count_ctx, cudaStream_t st);
+void sap_batch_free(SapBatchPlan* plan);
 
 // launch with programmatic stream serialization (see pdl_wait)
 template <typename... KArgs, typename... Args>

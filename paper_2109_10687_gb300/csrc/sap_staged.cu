@@ -39,7 +39,9 @@
 // and the halo copy (once per right-hand side, parity r & 1).
 
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "qcd_internal.cuh"
 
@@ -142,6 +144,7 @@ struct StagedArgs {
   int* status;                 // word 0: set to QCD_ERR_TIMEOUT if a wait gives up
   int extra_tx;                // testing: bytes the staging wait expects beyond its copies
   int extra_htx;               // testing: bytes the halo wait expects beyond its copy
+  const int* skip;             // if set and nonzero: this lattice has stopped iterating (ragged batch)
 };
 
 // ---------------------------------------------------------------------------
@@ -484,7 +487,7 @@ __device__ __forceinline__ void st_give_up(int* status, int tid, bool wait0, uin
 // independent streams of the same arithmetic.  The arithmetic per site is
 // the same in both; the autotuner picks the faster shape.
 template <bool HALF, typename SIO, int SPT>
-__global__ void __launch_bounds__(ST_THREADS / SPT, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF, SIO> a) {
+__device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, int blk) {
   constexpr int NT = ST_THREADS / SPT;
   extern __shared__ __align__(128) unsigned char smem[];
   using ST = StageT<HALF>;
@@ -495,9 +498,9 @@ __global__ void __launch_bounds__(ST_THREADS / SPT, HALF ? 2 : 1) sap_staged_ker
   uint64_t* cbar = lbar + 1;                                          // staged C_inv
   uint64_t* hbar = lbar + 2;                                          // halo copy
   const Geom& g = a.g;
-  if (loop_idle(g)) return;
+  if (loop_idle(g) || (a.skip && *(volatile const int*)a.skip)) return;
   const int tid = threadIdx.x;
-  const int dom = a.colour * g.nhalf + blockIdx.x;
+  const int dom = a.colour * g.nhalf + blk;
 
   // programmatic dependent launch: the next launch in the stream may start
   // its CTAs while this grid drains
@@ -641,6 +644,31 @@ __global__ void __launch_bounds__(ST_THREADS / SPT, HALF ? 2 : 1) sap_staged_ker
   }
 }
 
+template <bool HALF, typename SIO, int SPT>
+__global__ void __launch_bounds__(ST_THREADS / SPT, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF, SIO> a) {
+  sap_staged_body<HALF, SIO, SPT>(a, blockIdx.x);
+}
+
+// Ragged batch: one launch covers one half-sweep of every lattice.  Block b
+// belongs to lattice block_lat[b] and is its domain b - block_first[lat];
+// the block copies that lattice's arguments (geometry, kappa, field and
+// staging pointers) to shared memory first.  Every lattice must have 4^4
+// domains.
+template <bool HALF, typename SIO>
+__global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1)
+    sap_staged_batch_kernel(const StagedArgs<HALF, SIO>* __restrict__ tab, const int* __restrict__ block_lat,
+                            const int* __restrict__ block_first) {
+  __shared__ StagedArgs<HALF, SIO> sa;
+  const int lat = __ldg(block_lat + blockIdx.x);
+  {
+    const int* src = reinterpret_cast<const int*>(tab + lat);
+    int* dst = reinterpret_cast<int*>(&sa);
+    for (int k = threadIdx.x; k < (int)(sizeof(sa) / sizeof(int)); k += blockDim.x) dst[k] = __ldg(src + k);
+  }
+  __syncthreads();
+  sap_staged_body<HALF, SIO, 1>(sa, (int)blockIdx.x - __ldg(block_first + lat));
+}
+
 // ---------------------------------------------------------------------------
 // staging layouts, built from the internal layouts
 // ---------------------------------------------------------------------------
@@ -743,6 +771,7 @@ static void staged_sequence_shape(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, S
   // wait gives up and reports QCD_ERR_TIMEOUT
   a.extra_tx = ctx->inject == QCD_INJECT_STAGING_WAIT ? 16 : 0;
   a.extra_htx = ctx->inject == QCD_INJECT_HALO_WAIT ? 16 : 0;
+  a.skip = nullptr;
   for (int sweep = 0; sweep <= n_sap; ++sweep) {
     a.s_in32 = sweep == 0 ? s_first_in32 : F32Spinor{nullptr};
     a.do_update = sweep == n_sap ? 0 : 1;
@@ -810,6 +839,128 @@ void sap_staged_sequence_f16(qcd_ctx* ctx, F32Spinor s_first_in, F16Spinor s, F3
 void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F32Spinor x, F32Spinor b,
                               float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
   staged_sequence<true, F32Spinor>(ctx, s_first_in, s, x, b, F32Spinor{nullptr}, halo, nrhs, n_sap, n_jac, st);
+}
+
+// ---------------------------------------------------------------------------
+// ragged batch of lattices: M_SAP of every lattice in shared launches
+// ---------------------------------------------------------------------------
+struct SapBatchPlan {
+  int prec = 0;
+  int nlat = 0, nlaunch = 0;
+  int blocks = 0;                 // domains of one colour, summed over the lattices
+  void* d_tab = nullptr;          // StagedArgs [launch][lattice]
+  int* d_block_lat = nullptr;     // lattice of every block
+  int* d_block_first = nullptr;   // first block of every lattice
+};
+
+template <bool HALF, typename SIO>
+static void* sap_batch_table(const std::vector<SapLat>& L, int n_sap, int n_jac, int* status, const int* run_flag) {
+  static_assert(sizeof(StagedArgs<HALF, SIO>) % sizeof(int) == 0, "argument block is copied as ints");
+  const int n = (int)L.size(), nlaunch = 2 * (n_sap + 1);
+  std::vector<StagedArgs<HALF, SIO>> h((size_t)nlaunch * n);
+  for (int i = 0; i < n; ++i) {
+    const qcd_ctx* c = L[i].ctx;
+    StagedArgs<HALF, SIO> a;
+    std::memset(&a, 0, sizeof a);
+    a.g = c->geom;
+    a.g.run_flag = run_flag;
+    a.nrhs = 1;
+    a.n_jac = n_jac;
+    a.kappa = (float)c->kappa;
+    a.b = L[i].in;
+    a.halo = L[i].halo;
+    a.links = (const unsigned char*)(HALF ? c->st_link16 : c->st_link32);
+    a.clov = (const unsigned char*)(HALF ? c->st_clov16 : c->st_clov32);
+    a.status = status;
+    a.skip = L[i].skip;
+    SIO sv;
+    if constexpr (std::is_same<SIO, F16Spinor>::value) sv = F16Spinor{L[i].s16, L[i].s16n};
+    else sv = F32Spinor{L[i].s32};
+    a.s_in = sv;
+    a.s_out = sv;
+    int k = 0;
+    for (int sweep = 0; sweep <= n_sap; ++sweep) {
+      const bool last = sweep == n_sap;
+      for (int colour = 0; colour < 2; ++colour, ++k) {
+        a.s_in32 = sweep == 0 ? L[i].in : F32Spinor{nullptr};
+        a.do_update = last ? 0 : 1;
+        a.colour = colour;
+        a.do_surface = (sweep == 0 && colour == 0) ? 0 : 1;
+        a.do_halo = (last && colour == 1) ? 0 : 1;
+        if constexpr (std::is_same<SIO, F16Spinor>::value) {
+          a.x = F16Spinor{nullptr, nullptr};
+          a.x_out32 = last ? L[i].out : F32Spinor{nullptr};
+          a.x_store = 0;
+        } else {
+          a.x = L[i].out;
+          a.x_out32 = F32Spinor{nullptr};
+          a.x_store = last ? 1 : 0;
+        }
+        h[(size_t)k * n + i] = a;
+      }
+    }
+  }
+  void* d = nullptr;
+  QCD_CUDA_CHECK(cudaMalloc(&d, sizeof(StagedArgs<HALF, SIO>) * h.size()));
+  QCD_CUDA_CHECK(cudaMemcpy(d, h.data(), sizeof(StagedArgs<HALF, SIO>) * h.size(), cudaMemcpyHostToDevice));
+  QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_batch_kernel<HALF, SIO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      st_smem_bytes<HALF>()));
+  return d;
+}
+
+SapBatchPlan* sap_batch_plan(const std::vector<SapLat>& L, int sap_prec, int n_sap, int n_jac, int* status,
+                             const int* run_flag) {
+  for (const SapLat& l : L)
+    QCD_REQUIRE(sap_staged_available(l.ctx), QCD_ERR_ARG, "batched SAP: every lattice needs 4^4 domains");
+  SapBatchPlan* P = new SapBatchPlan();
+  try {
+    P->prec = sap_prec;
+    P->nlat = (int)L.size();
+    P->nlaunch = 2 * (n_sap + 1);
+    std::vector<int> lat, first;
+    for (int i = 0; i < P->nlat; ++i) {
+      first.push_back((int)lat.size());
+      for (int d = 0; d < L[i].ctx->geom.nhalf; ++d) lat.push_back(i);
+    }
+    P->blocks = (int)lat.size();
+    QCD_CUDA_CHECK(cudaMalloc(&P->d_block_lat, sizeof(int) * lat.size()));
+    QCD_CUDA_CHECK(cudaMemcpy(P->d_block_lat, lat.data(), sizeof(int) * lat.size(), cudaMemcpyHostToDevice));
+    QCD_CUDA_CHECK(cudaMalloc(&P->d_block_first, sizeof(int) * first.size()));
+    QCD_CUDA_CHECK(cudaMemcpy(P->d_block_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+    if (sap_prec == QCD_PREC_HALF) P->d_tab = sap_batch_table<true, F16Spinor>(L, n_sap, n_jac, status, run_flag);
+    else if (sap_prec == QCD_PREC_HALF_GAUGE)
+      P->d_tab = sap_batch_table<true, F32Spinor>(L, n_sap, n_jac, status, run_flag);
+    else P->d_tab = sap_batch_table<false, F32Spinor>(L, n_sap, n_jac, status, run_flag);
+  } catch (...) {
+    sap_batch_free(P);
+    throw;
+  }
+  return P;
+}
+
+void sap_batch_free(SapBatchPlan* P) {
+  if (!P) return;
+  if (P->d_tab) cudaFree(P->d_tab);
+  if (P->d_block_lat) cudaFree(P->d_block_lat);
+  if (P->d_block_first) cudaFree(P->d_block_first);
+  delete P;
+}
+
+template <bool HALF, typename SIO>
+static void sap_batch_launches(const SapBatchPlan* P, qcd_ctx* count_ctx, cudaStream_t st) {
+  const StagedArgs<HALF, SIO>* tab = static_cast<const StagedArgs<HALF, SIO>*>(P->d_tab);
+  for (int k = 0; k < P->nlaunch; ++k) {
+    LaunchScope ls(count_ctx, QCD_KC_SAP_BLOCK, st);
+    launch_pdl(sap_staged_batch_kernel<HALF, SIO>, dim3(P->blocks), dim3(ST_THREADS), st_smem_bytes<HALF>(), st,
+               tab + (size_t)k * P->nlat, (const int*)P->d_block_lat, (const int*)P->d_block_first);
+    check_launch();
+  }
+}
+
+void sap_batch_run(const SapBatchPlan* P, qcd_ctx* count_ctx, cudaStream_t st) {
+  if (P->prec == QCD_PREC_HALF) sap_batch_launches<true, F16Spinor>(P, count_ctx, st);
+  else if (P->prec == QCD_PREC_HALF_GAUGE) sap_batch_launches<true, F32Spinor>(P, count_ctx, st);
+  else sap_batch_launches<false, F32Spinor>(P, count_ctx, st);
 }
 
 }  // namespace qcd

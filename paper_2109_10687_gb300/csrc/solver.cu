@@ -24,24 +24,10 @@
 #include <mutex>
 #include <vector>
 
-#include "qcd_internal.cuh"
+#include "blas.cuh"
 
 namespace qcd {
 
-
-struct Scal {
-  double rho0_re, rho0_im;
-  double alpha_re, alpha_im;
-  double omega_re, omega_im;
-  double beta_re, beta_im;
-  double rnorm2, bnorm2;
-  double tol2;  // stop when rnorm2 < tol2 * bnorm2
-  double aux;
-  int done;     // 1: converged or failed; no further updates
-  int status;   // QCD_OK, QCD_ERR_BREAKDOWN, QCD_ERR_NONFINITE
-  int conv;     // 1: converged
-  int pad;
-};
 
 struct Workspace {
   int nrhs = 0;
@@ -98,8 +84,6 @@ void workspace_free(qcd_ctx* ctx) {
   ctx->ws = nullptr;
 }
 
-static constexpr int RED_THREADS = 256;
-static constexpr int MAX_RED_OUT = 4;
 
 // Allocate (or grow) the workspace for nrhs right-hand sides.  The reduction
 // buffers are always present; the solver vectors only with `solver`.
@@ -145,87 +129,11 @@ static Workspace* workspace(qcd_ctx* ctx, int nrhs, bool solver) {
   return w;
 }
 
-// ---------------------------------------------------------------------------
-// reduction machinery
-// ---------------------------------------------------------------------------
-template <int N>
-__device__ __forceinline__ void block_sum(double v[N], double* sh /* [32][N] */) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < N; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < N; ++k) sh[warp * N + k] = v[k];
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      v[k] = lane < nw ? sh[lane * N + k] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    }
-  }
-  __syncthreads();
-}
-
-// Writes this block's partials; returns true (in every thread) in the block
-// that finished last, which then holds the totals in tot[] (all threads).
-template <int N>
-__device__ bool grid_reduce(double v[N], double* partials, unsigned* counter, double tot[N]) {
-  __shared__ double sh[32 * N];
-  __shared__ bool is_last;
-  block_sum<N>(v, sh);
-  const int nb = gridDim.x;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) partials[blockIdx.x * N + k] = v[k];
-    __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
-    is_last = prev == (unsigned)(nb - 1);
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  double w[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) w[k] = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < N; ++k) w[k] += __ldcg(partials + i * N + k);
-  block_sum<N>(w, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) sh[k] = w[k];
-    *counter = 0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < N; ++k) tot[k] = sh[k];
-  __syncthreads();
-  return true;
-}
-
-// complex (a.x + i a.y) * (b.x + i b.y) for the two complex numbers of a float4
-__device__ __forceinline__ float4 caxpy4(float ar, float ai, float4 xv, float4 y) {
-  y.x = fmaf(ar, xv.x, fmaf(-ai, xv.y, y.x));
-  y.y = fmaf(ar, xv.y, fmaf(ai, xv.x, y.y));
-  y.z = fmaf(ar, xv.z, fmaf(-ai, xv.w, y.z));
-  y.w = fmaf(ar, xv.w, fmaf(ai, xv.z, y.w));
-  return y;
-}
-__device__ __forceinline__ void cdot_acc(float4 a, float4 b, float& re, float& im) {
-  re = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, re))));
-  im = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, im))));
-}
-__device__ __forceinline__ float norm4(float4 a) { return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w; }
-
 #define RHS_SETUP                                                     \
   const int rhs = blockIdx.y;                                         \
   Scal& sc = scal[rhs];                                               \
-  const size_t off = (size_t)rhs * n4;                                \
+  const size_t off = seg.at(rhs);                                     \
+  const size_t n4 = seg.size(rhs);                                    \
   double* part = partials + (size_t)rhs * MAX_RED_OUT * gridDim.x;    \
   unsigned* cnt = counters + rhs;
 
@@ -243,8 +151,9 @@ __global__ void k_norm2(const float4* __restrict__ a, size_t n4, double* out, do
 }
 
 // <a|b> -> out[2 rhs], out[2 rhs + 1]
-__global__ void k_cdot(const float4* __restrict__ a, const float4* __restrict__ b, size_t n4, double* out,
+__global__ void k_cdot(const float4* __restrict__ a, const float4* __restrict__ b, size_t n, double* out,
                        double* partials, unsigned* counters, Scal* scal) {
+  const Seg seg{n, nullptr, nullptr};
   RHS_SETUP
   (void)sc;
   float re = 0.f, im = 0.f;
@@ -258,7 +167,7 @@ __global__ void k_cdot(const float4* __restrict__ a, const float4* __restrict__ 
 }
 
 // BiCGStab initialisation: x = 0, r = p = rt = b, bnorm2 = |b|^2, rho_0 = bnorm2
-__global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float4* p, float4* rt, size_t n4,
+__global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float4* p, float4* rt, Seg seg,
                        double tol2, Scal* scal, double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   float s = 0.f;
@@ -277,6 +186,7 @@ __global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float
     sc.rho0_re = tot[0];
     sc.rho0_im = 0.0;
     sc.tol2 = tol2;
+    sc.iters = 0;
     sc.status = QCD_OK;
     sc.conv = tot[0] == 0.0;
     sc.done = tot[0] == 0.0;
@@ -289,7 +199,7 @@ __global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float
 }
 
 // alpha = rho_0 / <rt|q>
-__global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict__ q, size_t n4, Scal* scal,
+__global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict__ q, Seg seg, Scal* scal,
                         double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
@@ -298,6 +208,7 @@ __global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict_
     cdot_acc(rt[off + i], q[off + i], re, im);
   double v[2] = {re, im}, tot[2];
   if (grid_reduce<2>(v, part, cnt, tot) && threadIdx.x == 0) {
+    ++sc.iters;
     const double dn = tot[0] * tot[0] + tot[1] * tot[1];
     if (!(dn > 0.0) || !isfinite(dn)) {
       sc.status = isfinite(dn) ? QCD_ERR_BREAKDOWN : QCD_ERR_NONFINITE;
@@ -311,7 +222,7 @@ __global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict_
 }
 
 // x += alpha z; r -= alpha q; rnorm2 = |r|^2; first exit test
-__global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ q, size_t n4,
+__global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ q, Seg seg,
                           Scal* scal, double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
@@ -339,7 +250,7 @@ __global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, co
 }
 
 // omega = <t|r> / |t|^2
-__global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__ r, size_t n4, Scal* scal,
+__global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__ r, Seg seg, Scal* scal,
                         double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
@@ -365,7 +276,8 @@ __global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__
 // x += omega z; r -= omega t; rnorm2 = |r|^2, rho = <rt|r>; second exit test;
 // beta = alpha rho / (rho_0 omega); rho_0 = rho
 __global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ t,
-                          const float4* __restrict__ rt, size_t n4, Scal* scal, double* partials, unsigned* counters, int* ctrl) {
+                          const float4* __restrict__ rt, Seg seg, Scal* scal, double* partials, unsigned* counters,
+                          int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
   const float wr = (float)sc.omega_re, wi = (float)sc.omega_im;
@@ -410,12 +322,13 @@ __global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, co
 }
 
 // p = r + beta (p - omega q)
-__global__ void k_update_p(float4* p, const float4* __restrict__ r, const float4* __restrict__ q, size_t n4,
+__global__ void k_update_p(float4* p, const float4* __restrict__ r, const float4* __restrict__ q, Seg seg,
                            const Scal* scal) {
   const int rhs = blockIdx.y;
   const Scal& sc = scal[rhs];
   if (sc.done) return;
-  const size_t off = (size_t)rhs * n4;
+  const size_t off = seg.at(rhs);
+  const size_t n4 = seg.size(rhs);
   const float br = (float)sc.beta_re, bi = (float)sc.beta_im;
   const float wr = (float)sc.omega_re, wi = (float)sc.omega_im;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
@@ -668,8 +581,8 @@ static void bicg_half1(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_par
   const dim3 grid(w->nblocks, nrhs);
   am_sap(ctx, w, w->zp, w->q, w->p, nrhs, P.n_sap, P.n_jac, P.sap_prec, st);
   LaunchScope ls(ctx, QCD_KC_BLAS, st);
-  k_alpha<<<grid, RED_THREADS, 0, st>>>(w->rt, w->q, w->v4, w->scal, w->partials, w->counters, w->ctrl);
-  k_update1<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zp, w->q, w->v4, w->scal, w->partials, w->counters,
+  k_alpha<<<grid, RED_THREADS, 0, st>>>(w->rt, w->q, Seg{w->v4}, w->scal, w->partials, w->counters, w->ctrl);
+  k_update1<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zp, w->q, Seg{w->v4}, w->scal, w->partials, w->counters,
                                          w->ctrl);
   ctx->launches++;
   check_launch();
@@ -678,10 +591,10 @@ static void bicg_half2(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_par
   const dim3 grid(w->nblocks, nrhs);
   am_sap(ctx, w, w->zr, w->t, w->r, nrhs, P.n_sap, P.n_jac, P.sap_prec, st);
   LaunchScope ls(ctx, QCD_KC_BLAS, st);
-  k_omega<<<grid, RED_THREADS, 0, st>>>(w->t, w->r, w->v4, w->scal, w->partials, w->counters, w->ctrl);
-  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zr, w->t, w->rt, w->v4, w->scal, w->partials, w->counters,
+  k_omega<<<grid, RED_THREADS, 0, st>>>(w->t, w->r, Seg{w->v4}, w->scal, w->partials, w->counters, w->ctrl);
+  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zr, w->t, w->rt, Seg{w->v4}, w->scal, w->partials, w->counters,
                                          w->ctrl);
-  k_update_p<<<grid, RED_THREADS, 0, st>>>(w->p, w->r, w->q, w->v4, w->scal);
+  k_update_p<<<grid, RED_THREADS, 0, st>>>(w->p, w->r, w->q, Seg{w->v4}, w->scal);
   ctx->launches += 2;
   check_launch();
 }
@@ -707,7 +620,7 @@ static int bicgstab_sap(qcd_ctx* ctx, Workspace* w, const float4* b32, int nrhs,
   QCD_CUDA_CHECK(cudaMemcpyAsync(w->ctrl, w->h_ctrl, sizeof(int) * 3, cudaMemcpyHostToDevice, st));
   {
     LaunchScope ls(ctx, QCD_KC_BLAS, st);
-    k_init<<<grid, RED_THREADS, 0, st>>>(b32, w->x, w->r, w->p, w->rt, w->v4, P.inner_tol * P.inner_tol, w->scal,
+    k_init<<<grid, RED_THREADS, 0, st>>>(b32, w->x, w->r, w->p, w->rt, Seg{w->v4}, P.inner_tol * P.inner_tol, w->scal,
                                          w->partials, w->counters, w->ctrl);
     check_launch();
   }
