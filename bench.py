@@ -337,17 +337,20 @@ def run_kernel_case(args):
     lat = Lattice(dims, DOMAIN, -1, "chiral", "cuda:0").setup(random_su3_field(dims, EPS, GAUGE_SEED), KAPPA, CSW)
     b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, SOURCE_SEED))).cuda().contiguous()
     prec = B.PREC_DOUBLE if args.kernel == "dslash64" else B.PREC_SINGLE
-    a = lat.field("double" if prec == B.PREC_DOUBLE else "single")
-    o = lat.field("double" if prec == B.PREC_DOUBLE else "single")
-    B.qcd_import_spinor(lat.ctx, a, b, prec)
+    if args.shape is not None:
+        B.qcd_set_sap_shape(lat.ctx, args.shape)
+    nrhs = args.nrhs
+    a = lat.field("double" if prec == B.PREC_DOUBLE else "single", nrhs)
+    o = lat.field("double" if prec == B.PREC_DOUBLE else "single", nrhs)
+    B.qcd_import_spinor(lat.ctx, a, b.expand((nrhs,) + tuple(b.shape)).contiguous() if nrhs > 1 else b, prec, nrhs)
     for _ in range(args.reps):
         if args.kernel.startswith("sap"):
             sp = B.PREC_HALF if args.kernel == "sap16" else B.PREC_SINGLE
-            B.qcd_sap_apply(lat.ctx, o, a, N_SAP, N_JAC, sp, 0)
+            B.qcd_sap_apply_nrhs(lat.ctx, o, a, nrhs, N_SAP, N_JAC, sp, 0)
         else:
-            B.qcd_apply_D(lat.ctx, o, a, prec)
+            B.qcd_apply_D(lat.ctx, o, a, prec, nrhs=nrhs)
     torch.cuda.synchronize()
-    print(f"kernel case {args.kernel} on {dims}: {args.reps} applications done")
+    print(f"kernel case {args.kernel} on {dims}, {nrhs} right-hand sides: {args.reps} applications done")
     print(B.qcd_tuning_report(lat.ctx).strip())
     lat.close()
 
@@ -364,6 +367,8 @@ def main():
                     help="profiling case: set up the workload and run only REPS applications of one kernel")
     ap.add_argument("--lattice", type=int, default=32, help="lattice extent of the profiling case")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the profiling case")
+    ap.add_argument("--shape", type=int, default=None, help="fix the SAP block-kernel shape of the profiling case")
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5ragged", "n2"],
                     help="c2 (default) is the benchmark line; the others measure the other workloads")
     args = ap.parse_args()

@@ -361,6 +361,26 @@ int qcd_set_tuning(qcd_ctx* ctx, int enable);
  * Every shape computes the same M_SAP bit for bit.  QCD_ERR_ARG otherwise. */
 int qcd_set_sap_shape(qcd_ctx* ctx, int shape);
 
+/* Autotuner over SAP domain shapes, by time to solution.  The domain shape
+ * fixes a context's field layout, so for each candidate this creates a
+ * temporary context (dims, domain = candidate, bc_t, basis as qcd_create),
+ * sets U, kappa, c_SW, builds the clover term, solves D x = b once to warm
+ * it and once more timed (params as qcd_solve; NULL: defaults), and
+ * destroys it.  U and b are canonical float64 fields, both on the device
+ * (on_device = 1) or both in host memory.  candidates: n shapes of 4 ints;
+ * n = 0 (candidates may be NULL) takes the built-in list (4^4, 8x4x4x2,
+ * 2x4x4x8, 4x4x2x4, 8x8x2x2, 4x4x4x2, 2^4; qcd_tune_domain_default_count()
+ * of them).  A candidate that does not fit the lattice (see qcd_create) or
+ * whose solve does not reach params->tol is skipped.  best_domain receives
+ * the fastest shape; seconds (NULL, or one double per candidate) the timed
+ * solve of each, -1 for a skipped one.  Returns QCD_ERR_ARG if no candidate
+ * solved.  Allocates a temporary x (one field) and each candidate's context;
+ * synchronises the device's default stream. */
+int qcd_tune_domain(const int dims[4], int bc_t, int basis, const double* U, const double* b, int on_device,
+                    double kappa, double csw, const qcd_solve_params* params, const int* candidates, int n,
+                    int best_domain[4], double* seconds);
+int qcd_tune_domain_default_count(void);
+
 /* Text report of the tuned choices, one line per key:
  * "<key> <shape> <ms>", followed by the time of every shape tried. */
 int qcd_tuning_report(qcd_ctx* ctx, char* buf, size_t len);

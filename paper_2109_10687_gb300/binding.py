@@ -84,6 +84,10 @@ _SIGS = {
     "qcd_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "qcd_set_tuning": (_I, [_P, _I]),
     "qcd_set_sap_shape": (_I, [_P, _I]),
+    "qcd_tune_domain": (_I, [ctypes.POINTER(ctypes.c_int), _I, _I, _P, _P, _I, ctypes.c_double, ctypes.c_double,
+                             ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int), _I,
+                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "qcd_tune_domain_default_count": (_I, []),
     "qcd_batch_create": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "qcd_batch_destroy": (_I, [_P]),
     "qcd_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -292,6 +296,26 @@ def qcd_launch_count(ctx):
 
 def qcd_set_tuning(ctx, enable=True):
     return check(ctx, lib().qcd_set_tuning(ctx, int(bool(enable))))
+
+
+def qcd_tune_domain(dims, u, b, kappa, csw, params=None, candidates=None, bc_t=-1, basis=0):
+    """Time-to-solution autotuner over SAP domain shapes.  u, b: canonical
+    float64 (real-view) tensors or arrays, both on the device or both on the
+    host.  Returns (best_domain, {candidate: seconds or None})."""
+    p = params if params is not None else qcd_solve_params_default()
+    cands = [tuple(int(v) for v in c) for c in candidates] if candidates else None
+    n = len(cands) if cands else 0
+    flat = (ctypes.c_int * (4 * max(n, 1)))(*[v for c in (cands or []) for v in c])
+    nout = n if n else lib().qcd_tune_domain_default_count()
+    secs = (ctypes.c_double * nout)()
+    best = (ctypes.c_int * 4)()
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    rc = lib().qcd_tune_domain(d, int(bc_t), int(basis), _ptr(u), _ptr(b), _on_device(b), float(kappa), float(csw),
+                               ctypes.byref(p), flat if n else None, n, best, secs)
+    if rc != QCD_OK:
+        raise QcdError(rc, "qcd_tune_domain: no candidate solved")
+    keys = cands if cands else [None] * nout
+    return tuple(best), {k if k else i: (v if v >= 0 else None) for i, (k, v) in enumerate(zip(keys, secs))}
 
 
 def qcd_set_sap_shape(ctx, shape):

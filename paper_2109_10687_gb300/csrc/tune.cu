@@ -5,6 +5,10 @@
 // arithmetic each site performs.
 
 #include <algorithm>
+#include <array>
+#include <chrono>
+#include <cstdlib>
+#include <vector>
 #include <cstdio>
 #include <map>
 #include <string>
@@ -82,6 +86,75 @@ extern "C" int qcd_set_tuning(qcd_ctx* ctx, int enable) {
   if (!enable) tuner_of(ctx)->best.clear();
   return QCD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// domain-shape autotuner (time to solution)
+// ---------------------------------------------------------------------------
+// The SAP domain fixes the context's field layout, so each candidate shape
+// gets a temporary context: gauge field, parameters and clover term set up,
+// one solve to warm it (allocations and the kernel tuners), then one timed
+// solve.  A candidate that does not fit the lattice, or whose solve misses
+// the tolerance, is skipped (seconds = -1).
+static std::vector<std::array<int, 4>> default_domains() {
+  return {{4, 4, 4, 4}, {8, 4, 4, 2}, {2, 4, 4, 8}, {4, 4, 2, 4}, {8, 8, 2, 2}, {4, 4, 4, 2}, {2, 2, 2, 2}};
+}
+
+extern "C" int qcd_tune_domain(const int dims[4], int bc_t, int basis, const double* U, const double* b,
+                               int on_device, double kappa, double csw, const qcd_solve_params* params,
+                               const int* candidates, int n, int best_domain[4], double* seconds) {
+  if (!dims || !U || !b || !best_domain || n < 0 || (n > 0 && !candidates)) return QCD_ERR_ARG;
+  std::vector<std::array<int, 4>> cand;
+  if (n > 0) {
+    for (int k = 0; k < n; ++k)
+      cand.push_back({candidates[4 * k], candidates[4 * k + 1], candidates[4 * k + 2], candidates[4 * k + 3]});
+  } else {
+    cand = default_domains();
+  }
+  qcd_solve_params P;
+  if (params) P = *params;
+  else qcd_solve_params_default(&P);
+  long long vol = 1;
+  for (int mu = 0; mu < 4; ++mu) vol *= dims[mu];
+  const size_t bytes = (size_t)vol * 24 * sizeof(double);
+  double* x = nullptr;
+  if (on_device) {
+    if (cudaMalloc(&x, bytes) != cudaSuccess) return QCD_ERR_OOM;
+  } else {
+    x = static_cast<double*>(std::malloc(bytes));
+    if (!x) return QCD_ERR_OOM;
+  }
+  double best = -1.0;
+  int result = QCD_ERR_ARG;  // until some candidate succeeds
+  for (size_t k = 0; k < cand.size(); ++k) {
+    double t = -1.0;
+    qcd_ctx* c = nullptr;
+    if (qcd_create(dims, cand[k].data(), bc_t, basis, &c) == QCD_OK) {
+      int rc = qcd_set_gauge(c, U, on_device, 0.0, nullptr);
+      if (rc == QCD_OK) rc = qcd_set_params(c, kappa, csw);
+      if (rc == QCD_OK) rc = qcd_build_clover(c, nullptr);
+      qcd_solve_info info;
+      if (rc == QCD_OK) rc = qcd_solve(c, x, b, 1, on_device, &P, &info, nullptr);
+      if (rc == QCD_OK) {
+        const auto t0 = std::chrono::steady_clock::now();
+        rc = qcd_solve(c, x, b, 1, on_device, &P, &info, nullptr);
+        if (rc == QCD_OK) t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      }
+      qcd_destroy(c);
+    }
+    if (seconds && k < (size_t)(n > 0 ? n : (int)cand.size())) seconds[k] = t;
+    if (t >= 0.0 && (best < 0.0 || t < best)) {
+      best = t;
+      for (int mu = 0; mu < 4; ++mu) best_domain[mu] = cand[k][mu];
+      result = QCD_OK;
+    }
+  }
+  if (on_device) cudaFree(x);
+  else std::free(x);
+  cudaGetLastError();  // a rejected candidate leaves no error behind
+  return result;
+}
+
+extern "C" int qcd_tune_domain_default_count(void) { return (int)default_domains().size(); }
 
 extern "C" int qcd_set_sap_shape(qcd_ctx* ctx, int shape) {
   if (!ctx || shape < -1 || shape > 1) return QCD_ERR_ARG;

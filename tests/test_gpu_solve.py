@@ -58,6 +58,53 @@ def test_solve_residual_precisions(c1, c1_ref, residual_prec):
     assert rel_l2(x, x_ref) < 1e-8
 
 
+@pytest.mark.parametrize("kappa,seed", [(0.12, 1001), (0.125, 1002), (0.126, 1003)])
+def test_double_float_residual_bound(kappa, seed):
+    """Algorithm 4 with its residual r = b - D x in double-float (two float32,
+    about 48 significant bits, unit u = 2^-48): the residual the solver
+    reports, and stops on, differs from the float64 residual of the same x
+    (recomputed by the oracle) by at most the rounding of D x and of b:
+    |r_df - r_64| / |b| <= n_t u |D|_max |x| / |b| + u, with n_t = 100 terms
+    per component of D x (8 hops of 3x3 links, the clover blocks) and
+    |D|_max = 3 (1 + 8 kappa |U| (1 +- gamma) and 1 + C, 16 kappa < 2.1);
+    that is 300 u |x| / |b|.  At the tolerance 1e-10 this is a few 1e-12
+    relative error in the stopping test, the same order as the float64
+    residual's own rounding times the lattice's condition."""
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), eps=0.3, kappa=kappa, csw=1.0, seed=seed)
+    try:
+        b = gaussian_spinor(p.dims, seed + 1000)
+        x, rc, info = p.lat.solve(b, tol=1e-10, sap_prec="half", inner_tol=1e-5, residual_prec=0)
+        x = to_np(x)
+        assert rc == 0
+        r64 = true_resid(p.op, x, b)
+        assert r64 < 1e-10
+        u = 2.0 ** -48
+        bound = u + 300 * u * np.linalg.norm(x.ravel()) / np.linalg.norm(b.ravel())
+        assert abs(info.true_resid - r64) <= bound, (info.true_resid, r64, bound)
+        # the native float64 residual of the same solve agrees with the oracle to its own rounding
+        x1, rc1, info1 = p.lat.solve(b, tol=1e-10, sap_prec="half", inner_tol=1e-5, residual_prec=1)
+        assert rc1 == 0 and abs(info1.true_resid - true_resid(p.op, to_np(x1), b)) <= bound
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("shape", [0, 1, -1])
+def test_solve_with_each_sap_kernel_shape(c1, c1_ref, shape):
+    """The solve with each shape of the SAP block kernel (one or two sites
+    per thread, or the autotuned one) reaches the float64 true residual 1e-10
+    recomputed by the oracle, with the same iterations."""
+    from paper_2109_10687_gb300 import binding as B
+    b, x_ref = c1_ref
+    try:
+        B.qcd_set_sap_shape(c1.lat.ctx, shape)
+        x, rc, info = c1.lat.solve(b, tol=1e-10, sap_prec="half", inner_tol=1e-5)
+    finally:
+        B.qcd_set_sap_shape(c1.lat.ctx, -1)
+    assert rc == 0
+    assert true_resid(c1.op, to_np(x), b) < 1e-10
+    assert rel_l2(to_np(x), x_ref) < 1e-8
+
+
 def test_solve_host_buffers(c1, c1_ref):
     b, x_ref = c1_ref
     x, rc, info = c1.lat.solve(b, host=True, tol=1e-10)
