@@ -332,20 +332,22 @@ def _paper_flop_per_site_iter(domain, n_sap, n_jac, hops=(168, 168, 168, 168)):
 
 
 def n2(args):
-    """The paper's algorithm parameters (n_sap 4, n_jac 2, float32 SAP-BiCGStab)
-    on 32^4: BiCGStab iterations per second from the difference of two
-    fixed-length solves, and the rate in the paper's flop accounting.  Paper,
-    one A64FX node (4 processes): 1.38e7 site-iterations/s, 0.83 TFLOPS
-    (Table 2, first row).  With this build's 4^4 domains (the shared-memory
-    SAP kernel) and, as the nearest power-of-two analogue of the paper's
-    elongated 16x6x4x3 domains, 16x4x2x2 domains (the generic SAP kernel)."""
+    """The paper's algorithm parameters (n_sap 4, n_jac 2, float32 SAP-BiCGStab):
+    BiCGStab iterations per second from the difference of two fixed-length
+    solves, and the rate in the paper's flop accounting.  Paper, one A64FX
+    node (4 processes): 1.38e7 site-iterations/s, 0.83 TFLOPS (Table 2,
+    first row, 32x6x4x3 per process = two 16x6x4x3 domains).  Measured on
+    32^4 with 4^4 domains (the shared-memory block kernel), and on
+    64x24x32x24 both with the paper's own 16x6x4x3 SAP domains (the
+    general-domain kernel; fields stored in 4^4 blocks) and with 4^4
+    domains."""
     from lattice_inputs import gaussian_spinor
     from paper_2109_10687_gb300 import binding as B
-    dims, n_sap, n_jac = (32, 32, 32, 32), 4, 2
-    vol = int(np.prod(dims))
+    n_sap, n_jac = 4, 2
     out = {}
 
-    def rate(lat, prec, flop):
+    def rate(lat, dims, prec, flop, flop_paper_basis=None):
+        vol = int(np.prod(dims))
         b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2001))).cuda().contiguous()
         x = torch.zeros_like(b)
         times = {}
@@ -358,25 +360,41 @@ def n2(args):
             times[iters] = (t, info.inner_iters)
         (t1, i1), (t2, i2) = times[10], times[30]
         t_iter = (t2 - t1) / max(1, i2 - i1)
-        return {"ms_per_iteration": 1e3 * t_iter, "iterations": [i1, i2],
-                "site_iterations_per_s": vol / t_iter, "tflops_paper_accounting": flop * vol / t_iter / 1e12,
-                "vs_a64fx_node_site_iterations": vol / t_iter / 1.38e7}
+        r = {"lattice": list(dims), "ms_per_iteration": 1e3 * t_iter, "iterations": [i1, i2],
+             "site_iterations_per_s": vol / t_iter, "flop_per_site_iteration": flop,
+             "tflops_paper_accounting": flop * vol / t_iter / 1e12,
+             "vs_a64fx_node_site_iterations": vol / t_iter / 1.38e7}
+        if flop_paper_basis is not None:
+            r["flop_per_site_iteration_paper_basis"] = flop_paper_basis
+            r["tflops_paper_accounting_paper_basis"] = flop_paper_basis * vol / t_iter / 1e12
+        return r
 
-    domain = (4, 4, 4, 4)
+    # 32^4 on 4^4 domains (the shared-memory block kernel)
+    dims, domain = (32, 32, 32, 32), (4, 4, 4, 4)
     flop = _paper_flop_per_site_iter(domain, n_sap, n_jac)
-    out["flop_per_site_iteration"] = flop
     lat = _lat(dims, 0.3, 0.125, 1.0, 1001, domain)
     for name, prec in (("float32", "single"), ("float16_storage", "half")):
-        out[name] = rate(lat, prec, flop)
+        out[name] = rate(lat, dims, prec, flop)
     lat.close()
-    domain = (16, 4, 2, 2)
-    flop = _paper_flop_per_site_iter(domain, n_sap, n_jac)
-    lat = _lat(dims, 0.3, 0.125, 1.0, 1001, domain)
-    out["float32_domains_16x4x2x2"] = dict(rate(lat, "single", flop), flop_per_site_iteration=flop)
+    # 64x24x32x24: the paper's 16x6x4x3 domains, and 4^4 domains on the same lattice
+    dims = (64, 24, 32, 24)
+    lat = _lat(dims, 0.3, 0.125, 1.0, 1001, (4, 4, 4, 4))
+    out["float32_64x24x32x24_domains_4x4x4x4"] = rate(lat, dims, "single",
+                                                      _paper_flop_per_site_iter((4, 4, 4, 4), n_sap, n_jac))
+    paper = (16, 6, 4, 3)
+    B.qcd_set_sap_domain(lat.ctx, paper)
+    # chiral basis (168 flop for every hop, what the kernels compute) and the
+    # paper's basis (156 for a temporal hop), which reproduces Tables 2-3
+    out["float32_64x24x32x24_domains_16x6x4x3"] = rate(
+        lat, dims, "single", _paper_flop_per_site_iter(paper, n_sap, n_jac),
+        _paper_flop_per_site_iter(paper, n_sap, n_jac, hops=(168, 168, 168, 156)))
+    out["float16_gauge_64x24x32x24_domains_16x6x4x3"] = rate(
+        lat, dims, "half_gauge", _paper_flop_per_site_iter(paper, n_sap, n_jac),
+        _paper_flop_per_site_iter(paper, n_sap, n_jac, hops=(168, 168, 168, 156)))
     lat.close()
-    return {"config": {"workload": "32^4, eps 0.3, kappa 0.125, c_sw 1.0; SAP-BiCGStab with the paper's n_sap 4, "
-                                   "n_jac 2 on 4^4 domains and on 16x4x2x2 domains; fixed iteration counts "
-                                   "(graph loop)"},
+    return {"config": {"workload": "eps 0.3, kappa 0.125, c_sw 1.0; SAP-BiCGStab with the paper's n_sap 4, n_jac 2: "
+                                   "32^4 on 4^4 domains; 64x24x32x24 on the paper's 16x6x4x3 domains and on 4^4 "
+                                   "domains; fixed iteration counts (graph loop)"},
             "metric": "BiCGStab iterations: site-iterations/s and TFLOPS in the paper's flop accounting",
             "unit": "site-iterations/s", "results": out}
 

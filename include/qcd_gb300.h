@@ -210,6 +210,18 @@ int qcd_apply_A_block(qcd_ctx* ctx, void* out, const void* in, int row, int col,
 int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac, int sap_prec,
                   int with_A, void* stream);
 
+/* SAP domains independent of the context's storage blocking (Sec. 3; the
+ * paper's runs use 16x6x4x3 to 16x12x8x12 domains, Tables 2-3).  sdom[4]:
+ * extents of any size (not only powers of two) with every L_mu a multiple
+ * of 2 sdom_mu and at most 1152 sites per domain; NULL returns to the
+ * storage domains (the default).  With such domains every SAP application
+ * (qcd_sap_apply, qcd_sap_apply_nrhs, qcd_solve) runs Algorithms 1-2 on them
+ * with a kernel that holds one domain per CTA in shared memory (x and s in
+ * float32) and reads links and C_inv from the internal layouts; sap_prec
+ * must be QCD_PREC_SINGLE or QCD_PREC_HALF_GAUGE (QCD_ERR_ARG otherwise).
+ * Errors: QCD_ERR_ARG for a domain that does not fit. */
+int qcd_set_sap_domain(qcd_ctx* ctx, const int sdom[4]);
+
 /* qcd_sap_apply for nrhs stacked fields (in and out hold nrhs internal
  * float32 fields one after the other).  With 4^4 domains every right-hand
  * side goes through each block-kernel launch and shares its staged links and

@@ -84,6 +84,7 @@ _SIGS = {
     "qcd_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "qcd_set_tuning": (_I, [_P, _I]),
     "qcd_set_sap_shape": (_I, [_P, _I]),
+    "qcd_set_sap_domain": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "qcd_tune_domain": (_I, [ctypes.POINTER(ctypes.c_int), _I, _I, _P, _P, _I, ctypes.c_double, ctypes.c_double,
                              ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int), _I,
                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
@@ -316,6 +317,12 @@ def qcd_tune_domain(dims, u, b, kappa, csw, params=None, candidates=None, bc_t=-
         raise QcdError(rc, "qcd_tune_domain: no candidate solved")
     keys = cands if cands else [None] * nout
     return tuple(best), {k if k else i: (v if v >= 0 else None) for i, (k, v) in enumerate(zip(keys, secs))}
+
+
+def qcd_set_sap_domain(ctx, sdom):
+    """SAP domains of any extents, independent of the storage blocking (None: the storage domains)."""
+    arr = (ctypes.c_int * 4)(*[int(v) for v in sdom]) if sdom is not None else None
+    return check(ctx, lib().qcd_set_sap_domain(ctx, arr))
 
 
 def qcd_set_sap_shape(ctx, shape):

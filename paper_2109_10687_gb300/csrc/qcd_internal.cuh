@@ -670,6 +670,8 @@ struct qcd_ctx {
   void* st_clov32 = nullptr;
   bool force_generic_sap = false;  // testing: use the generic SAP kernel
   int sap_shape = -1;              // SAP block-kernel shape: -1 autotuned, 0 one site, 1 two sites per thread
+  bool sap_general = false;        // SAP on domains sap_dom, independent of the storage blocking
+  int sap_dom[4] = {0, 0, 0, 0};
   int inject = 0;                  // testing: QCD_INJECT_* fault (host-side, bounded)
   qcd::Workspace* ws = nullptr;
   qcd::Profiler* prof = nullptr;
@@ -756,6 +758,11 @@ void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F
 // generic kernel, or the face halo of the shared-memory kernel
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                       void* ws_s, void* ws_x16, void* ws_b16, cudaStream_t st);
+void workspace_reset_graphs(qcd_ctx* ctx);
+// SAP on the context's general domains (sap_dom, any extents up to 1152 sites)
+bool sap_domain_valid(const int dims[4], const int sdom[4]);
+void sap_general_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
+                       void* ws_s, cudaStream_t st);
 void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
 
 // dslash modes

@@ -270,6 +270,10 @@ static void sap_sequence(qcd_ctx* ctx, SIO s_first_in, SIO s, SIO x, F32Spinor b
 // C_inv; the generic kernel runs them one after the other.
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                       void* ws_s, void* ws_x16, void* ws_b16, cudaStream_t st) {
+  if (ctx->sap_general) {
+    sap_general_apply(ctx, x, b, nrhs, n_sap, n_jac, sap_prec, ws_s, st);
+    return;
+  }
   const Geom& g = ctx->geom;
   const bool staged = sap_staged_available(ctx) && !ctx->force_generic_sap;
   const size_t v = (size_t)g.vol;

@@ -66,6 +66,12 @@ struct Workspace {
   } graphs;
 };
 
+// drop the captured inner-loop graphs (their kernels depend on settings
+// such as the SAP domains)
+void workspace_reset_graphs(qcd_ctx* ctx) {
+  if (ctx->ws) ctx->ws->graphs.reset();
+}
+
 void workspace_free(qcd_ctx* ctx) {
   Workspace* w = ctx->ws;
   if (!w) return;

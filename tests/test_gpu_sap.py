@@ -183,3 +183,69 @@ def test_halo_wait_timeout_is_reported_and_context_survives():
         assert rel_l2(got, sap.msap(p.op, b, 4, 4)) <= 5e-3
     finally:
         p.close()
+
+
+@pytest.fixture(scope="module")
+def paper_domains():
+    """32x12x8x6 stored in 4x2x2x1 blocks, with the SAP on the paper's
+    16x6x4x3 domains (Sec. 4.3, Tables 2-3): two domains per direction."""
+    from paper_2109_10687_gb300 import binding as B
+    p = Problem((32, 12, 8, 6), (4, 2, 2, 1), eps=0.3, kappa=0.12, csw=1.0, seed=1121, oracle=False)
+    B.qcd_set_sap_domain(p.lat.ctx, (16, 6, 4, 3))
+    from oracle.dirac import CloverWilson
+    p.op = CloverWilson(p.u, 0.12, 1.0, p.gammas, bc_t=-1, domain=(16, 6, 4, 3))
+    yield p
+    p.close()
+
+
+@pytest.mark.parametrize("n_sap,n_jac", [(0, 1), (4, 2)])
+def test_msap_paper_domains_float32(paper_domains, n_sap, n_jac):
+    """M_SAP on non-power-of-two domains against the oracle's literal
+    Algorithm 1 on the same domains, at the paper's n_sap 4, n_jac 2."""
+    b = paper_domains.source(2130)
+    got = to_np(paper_domains.lat.sap(b, n_sap, n_jac, "single"))
+    ref = sap.msap(paper_domains.op, b, n_sap, n_jac)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_msap_paper_domains_float16_gauge(paper_domains):
+    b = paper_domains.source(2131)
+    got = to_np(paper_domains.lat.sap(b, 4, 2, "half_gauge"))
+    assert rel_l2(got, sap.msap(paper_domains.op, b, 4, 2)) <= 5e-3
+
+
+def test_am_sap_and_nrhs_paper_domains(paper_domains):
+    srcs = np.stack([paper_domains.source(2132 + r) for r in range(2)])
+    got = to_np(paper_domains.lat.sap(srcs, 1, 2, "single", with_A=True, nrhs=2))
+    for r in range(2):
+        assert rel_l2(got[r], sap.am_sap(paper_domains.op, srcs[r], 1, 2)) <= 1e-5
+
+
+def test_msap_general_domains_four_per_direction():
+    """8x6x4x3 domains on 32x12x8x6: four domains along x, so a domain's
+    forward and backward neighbours differ."""
+    from paper_2109_10687_gb300 import binding as B
+    from oracle.dirac import CloverWilson
+    p = Problem((32, 12, 8, 6), (4, 2, 2, 1), eps=0.3, kappa=0.12, csw=1.0, seed=1122, oracle=False)
+    try:
+        B.qcd_set_sap_domain(p.lat.ctx, (8, 6, 4, 3))
+        op = CloverWilson(p.u, 0.12, 1.0, p.gammas, bc_t=-1, domain=(8, 6, 4, 3))
+        b = p.source(2133)
+        assert rel_l2(to_np(p.lat.sap(b, 2, 2, "single")), sap.msap(op, b, 2, 2)) <= 1e-5
+        # back to the storage domains: the shared-nothing generic kernel on 4x2x2x1
+        B.qcd_set_sap_domain(p.lat.ctx, None)
+        op.set_domain((4, 2, 2, 1))
+        assert rel_l2(to_np(p.lat.sap(b, 1, 2, "single")), sap.msap(op, b, 1, 2)) <= 1e-5
+    finally:
+        p.close()
+
+
+def test_sap_domain_rejections(paper_domains):
+    from paper_2109_10687_gb300 import binding as B
+    ctx = paper_domains.lat.ctx
+    assert B.lib().qcd_set_sap_domain(ctx, (B.ctypes.c_int * 4)(16, 6, 4, 5)) == B.QCD_ERR_ARG
+    assert B.lib().qcd_set_sap_domain(ctx, (B.ctypes.c_int * 4)(32, 12, 8, 3)) == B.QCD_ERR_ARG  # 2 d must divide L
+    a = paper_domains.lat.field("single")
+    o = paper_domains.lat.field("single")
+    rc = B.lib().qcd_sap_apply(ctx, B._ptr(o), B._ptr(a), 1, 1, B.PREC_HALF, 0, None)
+    assert rc == B.QCD_ERR_ARG

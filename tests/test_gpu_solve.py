@@ -262,3 +262,24 @@ def test_solve_generic_domains(mixed_domains, sap_prec, use_graph):
     x = to_np(x)
     assert rc == 0 and info.true_resid < 1e-10
     assert true_resid(mixed_domains.op, x, b) < 1e-10
+
+
+@pytest.mark.parametrize("sap_prec", ["single", "half_gauge"])
+def test_solve_on_paper_sap_domains(sap_prec):
+    """The solve with the paper's algorithm parameters (n_sap 4, n_jac 2) on
+    its 16x6x4x3 SAP domains (Sec. 4.3), fields stored in 4x2x2x1 blocks:
+    float64 true residual below 1e-10, recomputed by the oracle."""
+    from paper_2109_10687_gb300 import binding as B
+    p = Problem((32, 12, 8, 6), (4, 2, 2, 1), eps=0.3, kappa=0.12, csw=1.0, seed=1131)
+    try:
+        B.qcd_set_sap_domain(p.lat.ctx, (16, 6, 4, 3))
+        b = gaussian_spinor(p.dims, 2131)
+        for use_graph in (0, 2):
+            x, rc, info = p.lat.solve(b, tol=1e-10, inner_tol=1e-6 if sap_prec == "single" else 1e-5, n_sap=4,
+                                      n_jac=2, sap_prec=sap_prec, use_graph=use_graph)
+            assert rc == 0 and true_resid(p.op, to_np(x), b) < 1e-10
+        # half (float16 vectors) is not offered on general domains
+        _, rc, _ = p.lat.solve(b, tol=1e-10, sap_prec="half", raise_on_error=False)
+        assert rc == B.QCD_ERR_ARG
+    finally:
+        p.close()
