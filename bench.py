@@ -363,6 +363,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-48", action="store_true", help="skip the 48^4 batched comparison")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged 32-lattice batch comparison")
     ap.add_argument("--kernel", choices=["sap16", "sap32", "dslash", "dslash64"], default=None,
                     help="profiling case: set up the workload and run only REPS applications of one kernel")
     ap.add_argument("--lattice", type=int, default=32, help="lattice extent of the profiling case")
@@ -620,6 +621,12 @@ def main():
         import bench_configs
         barrier()
         line["north_star_48x4"] = bench_configs.north_star_48x4(reps=1)
+        barrier()
+    if not args.no_ragged:
+        # the ragged batch of 32 lattices (8^4..16^4) in shared launches, against
+        # the same lattices as concurrent and as sequential solves
+        import bench_configs
+        line["ragged_batch_32"] = bench_configs.ragged_batch(reps=3, precs=("half",), dslash=False)
         barrier()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(iters={"inner": inner, "outer": outer})

@@ -31,6 +31,7 @@ struct Scal {
   int status;   // QCD_OK, QCD_ERR_BREAKDOWN, QCD_ERR_NONFINITE
   int conv;     // 1: converged
   int iters;   // iterations begun (counted by k_alpha)
+  int xpend;   // 1: x += alpha z_p of this iteration not yet applied (k_update2 or k_xfinal does it)
 };
 
 // Where element k of a stacked vector lives: uniform stacking (element k at
@@ -130,11 +131,12 @@ __global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, co
                           Scal* scal, double* partials, unsigned* counters, int* ctrl);
 __global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__ r, Seg seg, Scal* scal,
                         double* partials, unsigned* counters, int* ctrl);
-__global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ t,
-                          const float4* __restrict__ rt, Seg seg, Scal* scal, double* partials, unsigned* counters,
-                          int* ctrl);
+__global__ void k_update2(float4* x, float4* r, const float4* __restrict__ zp, const float4* __restrict__ z,
+                          const float4* __restrict__ t, const float4* __restrict__ rt, Seg seg, Scal* scal,
+                          double* partials, unsigned* counters, int* ctrl);
 __global__ void k_update_p(float4* p, const float4* __restrict__ r, const float4* __restrict__ q, Seg seg,
-                           const Scal* scal);
+                           Scal* scal);
+__global__ void k_xfinal(float4* x, const float4* __restrict__ z, Seg seg, const Scal* scal);
 __global__ void k_loop_cond(cudaGraphConditionalHandle handle, int* ctrl);
 
 }  // namespace qcd

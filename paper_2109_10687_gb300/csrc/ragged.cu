@@ -323,10 +323,18 @@ static void rg_half2(qcd_ctx* c0, RaggedWS* w, cudaStream_t st) {
   }
   LaunchScope ls(c0, QCD_KC_BLAS, st);
   k_omega<<<grid, RED_THREADS, 0, st>>>(w->t, w->r, seg, w->scal, w->partials, w->counters, w->ctrl);
-  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zr, w->t, w->rt, seg, w->scal, w->partials, w->counters,
-                                         w->ctrl);
+  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zp, w->zr, w->t, w->rt, seg, w->scal, w->partials,
+                                         w->counters, w->ctrl);
   k_update_p<<<grid, RED_THREADS, 0, st>>>(w->p, w->r, w->q, seg, w->scal);
   c0->launches += 2;
+  check_launch();
+}
+
+// the solution share x += alpha z_p of a lattice whose iteration stopped
+// after the first half (k_update1)
+static void rg_xfinal(qcd_ctx* c0, RaggedWS* w, cudaStream_t st) {
+  LaunchScope ls(c0, QCD_KC_BLAS, st);
+  k_xfinal<<<dim3(w->nblocks, w->n), RED_THREADS, 0, st>>>(w->x, w->zp, Seg{0, w->d_v4off, w->d_v4len}, w->scal);
   check_launch();
 }
 
@@ -382,6 +390,7 @@ static void rg_bicgstab(qcd_ctx* c0, RaggedWS* w, const qcd_solve_params& P, cud
       c0->launches = c_start;  // captured kernels are counted when replayed
     }
     QCD_CUDA_CHECK(cudaGraphLaunch(w->loop, st));
+    rg_xfinal(c0, w, st);
     QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_ctrl, w->ctrl, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(Scal) * w->n, cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaStreamSynchronize(st));
@@ -397,6 +406,9 @@ static void rg_bicgstab(qcd_ctx* c0, RaggedWS* w, const qcd_solve_params& P, cud
     rg_half2(c0, w, st);
     finished = rg_all_done(w, st);
   }
+  rg_xfinal(c0, w, st);
+  QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(Scal) * w->n, cudaMemcpyDeviceToHost, st));
+  QCD_CUDA_CHECK(cudaStreamSynchronize(st));
 }
 
 int ragged_solve(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp, double* const* x, const double* const* b,

@@ -193,6 +193,7 @@ __global__ void k_init(const float4* __restrict__ b, float4* x, float4* r, float
     sc.rho0_im = 0.0;
     sc.tol2 = tol2;
     sc.iters = 0;
+    sc.xpend = 0;
     sc.status = QCD_OK;
     sc.conv = tot[0] == 0.0;
     sc.done = tot[0] == 0.0;
@@ -227,21 +228,26 @@ __global__ void k_alpha(const float4* __restrict__ rt, const float4* __restrict_
   }
 }
 
-// x += alpha z; r -= alpha q; rnorm2 = |r|^2; first exit test
+// r -= alpha q; rnorm2 = |r|^2; first exit test.  The solution's share
+// x += alpha z_p is left pending and applied with the second one in
+// k_update2 (one pass over x instead of two), or by k_xfinal when the
+// iteration stops here.
 __global__ void k_update1(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ q, Seg seg,
                           Scal* scal, double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
   if (sc.done) return;
+  (void)x;
+  (void)z;
   const float ar = (float)sc.alpha_re, ai = (float)sc.alpha_im;
   float s = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-    x[off + i] = caxpy4(ar, ai, z[off + i], x[off + i]);
     const float4 rv = caxpy4(-ar, -ai, q[off + i], r[off + i]);
     r[off + i] = rv;
     s += norm4(rv);
   }
   double v[1] = {s}, tot[1];
   if (grid_reduce<1>(v, part, cnt, tot) && threadIdx.x == 0) {
+    sc.xpend = 1;
     sc.rnorm2 = tot[0];
     if (!isfinite(tot[0])) {
       sc.status = QCD_ERR_NONFINITE;
@@ -279,17 +285,26 @@ __global__ void k_omega(const float4* __restrict__ t, const float4* __restrict__
   }
 }
 
-// x += omega z; r -= omega t; rnorm2 = |r|^2, rho = <rt|r>; second exit test;
-// beta = alpha rho / (rho_0 omega); rho_0 = rho
-__global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, const float4* __restrict__ t,
-                          const float4* __restrict__ rt, Seg seg, Scal* scal, double* partials, unsigned* counters,
-                          int* ctrl) {
+// x += alpha z_p + omega z_r (z_p: zp, z_r: z); r -= omega t;
+// rnorm2 = |r|^2, rho = <rt|r>; second exit test;
+// beta = alpha rho / (rho_0 omega); rho_0 = rho.  A right-hand side that
+// stopped after k_update1 (converged or broken down since) gets only its
+// pending x += alpha z_p.
+__global__ void k_update2(float4* x, float4* r, const float4* __restrict__ zp, const float4* __restrict__ z,
+                          const float4* __restrict__ t, const float4* __restrict__ rt, Seg seg, Scal* scal,
+                          double* partials, unsigned* counters, int* ctrl) {
   RHS_SETUP
-  if (sc.done) return;
+  const float ar = (float)sc.alpha_re, ai = (float)sc.alpha_im;
+  if (sc.done) {
+    if (!sc.xpend) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+      x[off + i] = caxpy4(ar, ai, zp[off + i], x[off + i]);
+    return;
+  }
   const float wr = (float)sc.omega_re, wi = (float)sc.omega_im;
   float s = 0.f, re = 0.f, im = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-    x[off + i] = caxpy4(wr, wi, z[off + i], x[off + i]);
+    x[off + i] = caxpy4(wr, wi, z[off + i], caxpy4(ar, ai, zp[off + i], x[off + i]));
     const float4 rv = caxpy4(-wr, -wi, t[off + i], r[off + i]);
     r[off + i] = rv;
     s += norm4(rv);
@@ -327,11 +342,12 @@ __global__ void k_update2(float4* x, float4* r, const float4* __restrict__ z, co
   }
 }
 
-// p = r + beta (p - omega q)
+// p = r + beta (p - omega q); the pending x update has been applied by k_update2
 __global__ void k_update_p(float4* p, const float4* __restrict__ r, const float4* __restrict__ q, Seg seg,
-                           const Scal* scal) {
+                           Scal* scal) {
   const int rhs = blockIdx.y;
-  const Scal& sc = scal[rhs];
+  Scal& sc = scal[rhs];
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc.xpend = 0;  // no block of this kernel reads it
   if (sc.done) return;
   const size_t off = seg.at(rhs);
   const size_t n4 = seg.size(rhs);
@@ -341,6 +357,19 @@ __global__ void k_update_p(float4* p, const float4* __restrict__ r, const float4
     const float4 tmp = caxpy4(-wr, -wi, q[off + i], p[off + i]);
     p[off + i] = caxpy4(br, bi, tmp, r[off + i]);
   }
+}
+
+// x += alpha z_p for a right-hand side whose iteration stopped after
+// k_update1 (the loop left before k_update2); no-op otherwise
+__global__ void k_xfinal(float4* x, const float4* __restrict__ z, Seg seg, const Scal* scal) {
+  const int rhs = blockIdx.y;
+  const Scal& sc = scal[rhs];
+  if (!sc.xpend) return;
+  const size_t off = seg.at(rhs);
+  const size_t n4 = seg.size(rhs);
+  const float ar = (float)sc.alpha_re, ai = (float)sc.alpha_im;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    x[off + i] = caxpy4(ar, ai, z[off + i], x[off + i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -598,7 +627,8 @@ static void bicg_half2(qcd_ctx* ctx, Workspace* w, int nrhs, const qcd_solve_par
   am_sap(ctx, w, w->zr, w->t, w->r, nrhs, P.n_sap, P.n_jac, P.sap_prec, st);
   LaunchScope ls(ctx, QCD_KC_BLAS, st);
   k_omega<<<grid, RED_THREADS, 0, st>>>(w->t, w->r, Seg{w->v4}, w->scal, w->partials, w->counters, w->ctrl);
-  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zr, w->t, w->rt, Seg{w->v4}, w->scal, w->partials, w->counters,
+  k_update2<<<grid, RED_THREADS, 0, st>>>(w->x, w->r, w->zp, w->zr, w->t, w->rt, Seg{w->v4}, w->scal, w->partials,
+                                         w->counters,
                                          w->ctrl);
   k_update_p<<<grid, RED_THREADS, 0, st>>>(w->p, w->r, w->q, Seg{w->v4}, w->scal);
   ctx->launches += 2;
@@ -692,8 +722,16 @@ static int bicgstab_sap(qcd_ctx* ctx, Workspace* w, const float4* b32, int nrhs,
     G.kappa = ctx->kappa;
   }
   int it = 0;
+  // x += alpha z_p of a right-hand side whose iteration stopped after the
+  // first half (k_update1); the loop leaves that share to k_update2
+  auto xfinal = [&]() {
+    LaunchScope ls(ctx, QCD_KC_BLAS, st);
+    k_xfinal<<<grid, RED_THREADS, 0, st>>>(w->x, w->zp, Seg{w->v4}, w->scal);
+    check_launch();
+  };
   if (mode == 2) {
     QCD_CUDA_CHECK(cudaGraphLaunch(G.loop, st));
+    xfinal();
     QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_ctrl, w->ctrl, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(Scal) * nrhs, cudaMemcpyDeviceToHost, st));
     QCD_CUDA_CHECK(cudaStreamSynchronize(st));
@@ -718,6 +756,9 @@ static int bicgstab_sap(qcd_ctx* ctx, Workspace* w, const float4* b32, int nrhs,
       }
       finished = all_done(w, nrhs, st);
     }
+    xfinal();
+    QCD_CUDA_CHECK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(Scal) * nrhs, cudaMemcpyDeviceToHost, st));
+    QCD_CUDA_CHECK(cudaStreamSynchronize(st));
   }
   int worst = QCD_OK;
   for (int r = 0; r < nrhs; ++r) {
