@@ -367,10 +367,15 @@ int qcd_profile_read(qcd_ctx* ctx, int kernel_class, long long* launches, double
  * then used). */
 int qcd_set_tuning(qcd_ctx* ctx, int enable);
 
-/* Fix the SAP block kernel's shape for 4^4 domains: -1 autotuned (default),
+/* Fix the SAP kernel's shape: -1 autotuned (default).  For 4^4 domains:
  * 0 one site per thread (256 threads per domain), 1 two sites per thread
- * (128 threads per domain, each thread two independent site streams).
- * Every shape computes the same M_SAP bit for bit.  QCD_ERR_ARG otherwise. */
+ * (128 threads per domain, each thread two independent site streams); every
+ * shape computes the same M_SAP bit for bit.  For domains set with
+ * qcd_set_sap_domain and float16 links and C_inv (QCD_PREC_HALF_GAUGE):
+ * 0 one thread-block cluster per domain, one CTA per time slice (at most 8
+ * slices of at most 448 sites), links and C_inv staged in shared memory and
+ * the time hops between slices through distributed shared memory; 1 one CTA
+ * per domain reading links and C_inv through L1.  QCD_ERR_ARG otherwise. */
 int qcd_set_sap_shape(qcd_ctx* ctx, int shape);
 
 /* Autotuner over SAP domain shapes, by time to solution.  The domain shape

@@ -382,7 +382,8 @@ extern "C" int qcd_destroy(qcd_ctx* ctx) {
   tuner_free(ctx);
   void* ptrs[] = {ctx->d_nbr, ctx->d_lex2dom, ctx->d_tflag, ctx->u64, ctx->u32, ctx->u16, ctx->clov64,
                   ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status,
-                  ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32, ctx->udf, ctx->clovdf};
+                  ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32, ctx->udf, ctx->clovdf,
+                  ctx->cl_link, ctx->cl_clov};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
@@ -467,6 +468,7 @@ extern "C" int qcd_build_clover(qcd_ctx* ctx, void* stream) {
   QCD_CUDA_CHECK(cudaStreamSynchronize(st));
   QCD_REQUIRE(hs == 0, QCD_ERR_NONFINITE, "qcd_build_clover: singular or non-finite clover block");
   ctx->have_clover = true;
+  ++ctx->clover_gen;
   QCD_API_END(ctx)
 }
 

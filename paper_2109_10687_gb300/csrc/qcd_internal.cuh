@@ -672,6 +672,11 @@ struct qcd_ctx {
   int sap_shape = -1;              // SAP block-kernel shape: -1 autotuned, 0 one site, 1 two sites per thread
   bool sap_general = false;        // SAP on domains sap_dom, independent of the storage blocking
   int sap_dom[4] = {0, 0, 0, 0};
+  int clover_gen = 0;              // counts clover builds (staging copies follow it)
+  void* cl_link = nullptr;         // staging of the cluster SAP kernel (domains sap_dom)
+  void* cl_clov = nullptr;
+  int cl_gen = -1;
+  int cl_dom[4] = {0, 0, 0, 0};
   int inject = 0;                  // testing: QCD_INJECT_* fault (host-side, bounded)
   qcd::Workspace* ws = nullptr;
   qcd::Profiler* prof = nullptr;
@@ -763,6 +768,10 @@ void workspace_reset_graphs(qcd_ctx* ctx);
 bool sap_domain_valid(const int dims[4], const int sdom[4]);
 void sap_general_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                        void* ws_s, cudaStream_t st);
+// the same with one thread-block cluster per domain (float16 links and C_inv staged in shared memory)
+bool sap_cluster_eligible(const qcd_ctx* ctx, int sap_prec);
+void sap_cluster_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, void* ws_s,
+                       cudaStream_t st);
 void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);
 
 // dslash modes

@@ -22,6 +22,8 @@
 // The hops that stay inside the domain branch on the local coordinate (the
 // domain's sites are spread over the warps without regard to direction).
 
+#include <cstdio>
+
 #include "qcd_internal.cuh"
 
 namespace qcd {
@@ -293,21 +295,47 @@ bool sap_domain_valid(const int dims[4], const int sdom[4]) {
 
 // M_SAP for nrhs stacked float32 fields with the context's general SAP
 // domains; float32 (sap_prec SINGLE) or float16 links and C_inv with float32
-// vectors (HALF_GAUGE).  ws_s holds s (float32), one field per rhs.
+// vectors (HALF_GAUGE).  ws_s holds s (float32), one field per rhs.  With
+// float16 links and C_inv and domains whose time slices fit a CTA, the
+// cluster kernel (sap_cluster.cu, shape 0) and this one (shape 1) are both
+// available and the autotuner picks one; otherwise this kernel runs.
+static const char* const kGeneralShapes[] = {"cluster_per_domain", "cta_per_domain"};
+
 void sap_general_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                        void* ws_s, cudaStream_t st) {
   QCD_REQUIRE(sap_prec == QCD_PREC_SINGLE || sap_prec == QCD_PREC_HALF_GAUGE, QCD_ERR_ARG,
               "SAP on general domains: sap_prec must be SINGLE or HALF_GAUGE");
+  const bool can_cluster = sap_cluster_eligible(ctx, sap_prec);
   const size_t v4 = (size_t)ctx->geom.vol * 6;
-  for (int r = 0; r < nrhs; ++r) {
-    F32Spinor xs{x + r * v4}, bs{(float4*)b + r * v4}, ss{(float4*)ws_s + r * v4};
-    if (sap_prec == QCD_PREC_SINGLE)
-      general_sequence<LinkPtr<float>, CloverPtrF32, CloverBlockF32>(ctx, bs, ss, xs, bs, LinkPtr<float>{ctx->u32},
-                                                                     CloverPtrF32{ctx->cinv32}, n_sap, n_jac, st);
-    else
-      general_sequence<LinkPtrHalf, CloverPtrF16, CloverBlockF32>(ctx, bs, ss, xs, bs, LinkPtrHalf{ctx->u16},
-                                                                   CloverPtrF16{ctx->cinv16}, n_sap, n_jac, st);
+  auto run = [&](int v) {
+    if (v == 0 && can_cluster) {
+      sap_cluster_apply(ctx, x, b, nrhs, n_sap, n_jac, ws_s, st);
+      return;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+      F32Spinor xs{x + r * v4}, bs{(float4*)b + r * v4}, ss{(float4*)ws_s + r * v4};
+      if (sap_prec == QCD_PREC_SINGLE)
+        general_sequence<LinkPtr<float>, CloverPtrF32, CloverBlockF32>(ctx, bs, ss, xs, bs, LinkPtr<float>{ctx->u32},
+                                                                       CloverPtrF32{ctx->cinv32}, n_sap, n_jac, st);
+      else
+        general_sequence<LinkPtrHalf, CloverPtrF16, CloverBlockF32>(ctx, bs, ss, xs, bs, LinkPtrHalf{ctx->u16},
+                                                                     CloverPtrF16{ctx->cinv16}, n_sap, n_jac, st);
+    }
+  };
+  int v = ctx->sap_shape;
+  if (v < 0) {
+    if (can_cluster) {
+      const Geom& g = ctx->geom;
+      char key[160];
+      std::snprintf(key, sizeof key, "sap_general_f16gauge L%dx%dx%dx%d dom%dx%dx%dx%d nrhs%d n_sap%d n_jac%d", g.L[0],
+                    g.L[1], g.L[2], g.L[3], ctx->sap_dom[0], ctx->sap_dom[1], ctx->sap_dom[2], ctx->sap_dom[3], nrhs,
+                    n_sap, n_jac);
+      v = tune_pick(ctx, key, 2, kGeneralShapes, run, st);
+    } else {
+      v = 1;
+    }
   }
+  run(v);
 }
 
 }  // namespace qcd

@@ -249,3 +249,68 @@ def test_sap_domain_rejections(paper_domains):
     o = paper_domains.lat.field("single")
     rc = B.lib().qcd_sap_apply(ctx, B._ptr(o), B._ptr(a), 1, 1, B.PREC_HALF, 0, None)
     assert rc == B.QCD_ERR_ARG
+
+
+def _half_round(a):
+    return a.real.astype(np.float16).astype(np.float64) + 1j * a.imag.astype(np.float16).astype(np.float64)
+
+
+@pytest.mark.parametrize("dims,sdom", [((32, 12, 8, 6), (16, 6, 4, 3)), ((32, 12, 8, 6), (8, 6, 4, 3)),
+                                       ((32, 12, 8, 12), (8, 6, 4, 6))])
+def test_cluster_sap_kernel_on_general_domains(dims, sdom):
+    """The thread-block-cluster SAP kernel (one CTA per time slice of a
+    domain, the t hops between slices through distributed shared memory,
+    float16 links and C_inv staged in shared memory) gives M_SAP bit for bit
+    equal to the one-CTA-per-domain kernel (same float16 operator, same
+    arithmetic order), and matches the oracle's literal Algorithm 1 on the
+    same float16-rounded links and C_inv to 1e-5, with 3 and 6 slices per
+    domain."""
+    import copy
+    from paper_2109_10687_gb300 import binding as B
+    from oracle.dirac import CloverWilson
+    p = Problem(dims, (4, 2, 2, 1), eps=0.3, kappa=0.12, csw=1.0, seed=1151, oracle=False)
+    try:
+        B.qcd_set_sap_domain(p.lat.ctx, sdom)
+        op = CloverWilson(p.u, 0.12, 1.0, p.gammas, bc_t=-1, domain=sdom)
+        op16 = copy.copy(op)
+        op16.u = _half_round(op.u)
+        op16.cinv = _half_round(op.cinv)
+        b = p.source(2160)
+        out = {}
+        for shape in (0, 1):
+            B.qcd_set_sap_shape(p.lat.ctx, shape)
+            out[shape] = to_np(p.lat.sap(b, 2, 2, "half_gauge"))
+        B.qcd_set_sap_shape(p.lat.ctx, -1)
+        assert np.array_equal(out[0], out[1])
+        assert rel_l2(out[0], sap.msap(op16, b, 2, 2)) <= 1e-5
+        rep = B.qcd_tuning_report(p.lat.ctx)
+        tuned = to_np(p.lat.sap(b, 2, 2, "half_gauge"))
+        assert np.array_equal(tuned, out[0])
+        assert "cluster_per_domain" in B.qcd_tuning_report(p.lat.ctx) or "cluster_per_domain" in rep
+    finally:
+        p.close()
+
+
+def test_cluster_sap_wait_timeout_is_reported_and_context_survives():
+    """The failure path of the cluster kernel's bounded staging wait, without a
+    GPU fault: the test hook makes every CTA's wait expect 16 bytes that no
+    copy brings; the CTAs of a cluster agree through distributed shared memory
+    that a wait gave up, record QCD_ERR_TIMEOUT and leave together; the status
+    reaches the host and the same context then computes M_SAP correctly."""
+    from paper_2109_10687_gb300 import binding as B
+    p = Problem((32, 12, 8, 6), (4, 2, 2, 1), eps=0.3, kappa=0.12, csw=1.0, seed=1152)
+    try:
+        B.qcd_set_sap_domain(p.lat.ctx, (16, 6, 4, 3))
+        B.qcd_set_sap_shape(p.lat.ctx, 0)
+        b = p.source(2161)
+        B.qcd_test_inject(p.lat.ctx, B.INJECT_STAGING_WAIT)
+        p.lat.sap(b, 0, 1, "half_gauge")
+        assert B.qcd_device_status(p.lat.ctx, reset=True) == B.QCD_ERR_TIMEOUT
+        B.qcd_test_inject(p.lat.ctx, B.INJECT_NONE)
+        got = to_np(p.lat.sap(b, 1, 2, "half_gauge"))
+        assert B.qcd_device_status(p.lat.ctx) == B.QCD_OK
+        from oracle.dirac import CloverWilson
+        op = CloverWilson(p.u, 0.12, 1.0, p.gammas, bc_t=-1, domain=(16, 6, 4, 3))
+        assert rel_l2(got, sap.msap(op, b, 1, 2)) <= 5e-3
+    finally:
+        p.close()
