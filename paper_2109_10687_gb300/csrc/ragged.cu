@@ -58,6 +58,7 @@ struct RaggedWS {
   cudaGraphExec_t loop = nullptr;
   long long nloop = 0;
   cudaStream_t st = nullptr;
+  std::vector<int> clover_gen;  // each lattice's clover build the descriptors were made from
 };
 
 void ragged_free(RaggedWS* w) {
@@ -181,7 +182,16 @@ __global__ void __launch_bounds__(128) k_rg_axpy(const LatDesc* __restrict__ des
 // host side
 // ---------------------------------------------------------------------------
 static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
-  if (wp) return wp;
+  if (wp) {
+    // descriptors and SAP plans hold kappa and pointers taken at the first
+    // solve: rebuild them after any lattice's clover term was rebuilt
+    bool same = true;
+    for (size_t i = 0; i < ctx.size(); ++i) same = same && wp->clover_gen[i] == ctx[i]->clover_gen;
+    if (same) return wp;
+    QCD_CUDA_CHECK(cudaDeviceSynchronize());
+    ragged_free(wp);
+    wp = nullptr;
+  }
   RaggedWS* w = new RaggedWS();
   try {
     const int n = (int)ctx.size();
@@ -259,6 +269,7 @@ static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
     QCD_CUDA_CHECK(cudaMalloc(&w->d_site_lat, sizeof(int) * site_lat.size()));
     QCD_CUDA_CHECK(cudaMemcpy(w->d_site_lat, site_lat.data(), sizeof(int) * site_lat.size(), cudaMemcpyHostToDevice));
     QCD_CUDA_CHECK(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
+    for (const qcd_ctx* c : ctx) w->clover_gen.push_back(c->clover_gen);
   } catch (...) {
     ragged_free(w);
     throw;

@@ -167,3 +167,29 @@ def test_batch_solve_iteration_limit_reports_status(batch):
     rc, infos, xs, bs = _solve_batch(bt, probs, 6600, sap_prec=B.PREC_HALF, max_outer=1, max_inner=2)
     assert rc == B.QCD_ERR_NOT_CONVERGED
     assert all(i.status == B.QCD_ERR_NOT_CONVERGED and i.outer_iters == 1 for i in infos)
+
+
+def test_batch_solve_follows_a_new_kappa(batch):
+    """After a lattice's kappa changes (qcd_set_params + qcd_build_clover), the
+    next shared-launch solve uses the new operator: the oracle residual with
+    the new kappa is below 1e-10 for every lattice."""
+    from paper_2109_10687_gb300 import binding as B
+    from oracle.dirac import CloverWilson
+    probs, bt = batch
+    p0 = probs[0]
+    old_kappa = p0.kappa
+    new_kappa = 0.110
+    try:
+        B.qcd_set_params(p0.lat.ctx, new_kappa, p0.csw)
+        B.qcd_build_clover(p0.lat.ctx)
+        rc, infos, xs, bs = _solve_batch(bt, probs, 6700, sap_prec=B.PREC_HALF)
+        assert rc == 0
+        op_new = CloverWilson(p0.u, new_kappa, p0.csw, p0.gammas, bc_t=-1)
+        xn = to_np(torch.view_as_complex(xs[0]))
+        bn = to_np(torch.view_as_complex(bs[0]))
+        assert np.linalg.norm((bn - op_new.D(xn)).ravel()) / np.linalg.norm(bn.ravel()) < 1e-10
+        for p, x, b in zip(probs[1:], xs[1:], bs[1:]):
+            assert _oracle_resid(p, x, b) < 1e-10
+    finally:
+        B.qcd_set_params(p0.lat.ctx, old_kappa, p0.csw)
+        B.qcd_build_clover(p0.lat.ctx)
