@@ -297,8 +297,9 @@ int qcd_batch_apply_D(qcd_batch* batch, void* const* out, const void* const* in,
 
 /* Solve D_i x_i = b_i for every lattice (one right-hand side each, canonical
  * float64 fields as in qcd_solve; Algorithm 4 around Algorithm 5 on
- * A M_SAP, Sec. 3).  When every lattice has 4^4 domains, outer_restart = 0
- * and residual_prec = 1, the lattices are solved in SHARED LAUNCHES: each
+ * A M_SAP, Sec. 3).  When every lattice has 4^4 domains (and no SAP domains
+ * of its own, see qcd_set_sap_domain), outer_restart = 0 and
+ * residual_prec = 1, the lattices are solved in SHARED LAUNCHES: each
  * SAP half-sweep (Algorithm 1), each application of A and of the float64 D,
  * and each fused BLAS-1 step of Algorithm 5 is one kernel launch over every
  * lattice, through work lists built on the first call; the inner loop is one

@@ -81,7 +81,7 @@ void ragged_free(RaggedWS* w) {
 bool ragged_eligible(const std::vector<qcd_ctx*>& ctx, const qcd_solve_params& P) {
   if (P.outer_restart != 0 || P.residual_prec != 1) return false;
   for (const qcd_ctx* c : ctx)
-    if (!c->have_gauge || !c->have_clover || !sap_staged_available(c)) return false;
+    if (!c->have_gauge || !c->have_clover || !sap_staged_available(c) || c->sap_general) return false;
   return true;
 }
 
