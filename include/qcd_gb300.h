@@ -18,6 +18,8 @@
  *   power of two, dx*dy*dz*dt <= 256, and every L_mu is a multiple of 2*d_mu
  *   (an even number of domains per direction keeps the red/black colouring
  *   of Sec. 3 consistent across the periodic boundary).  Default domain 4^4.
+ *   The domains are the blocks the fields are stored in and, by default, the
+ *   SAP domains; qcd_set_sap_domain gives the SAP domains of any extents.
  * - Boundary conditions: periodic in x, y, z; bc_t = +1 (periodic) or -1
  *   (antiperiodic) in t, applied as a sign on every hop across t = Lt-1 <-> 0.
  * - CANONICAL layout (host or device, float64, little endian, x fastest):
