@@ -333,8 +333,12 @@ def run_kernel_case(args):
     from paper_2109_10687_gb300 import binding as B
     from paper_2109_10687_gb300.lattice import Lattice
     torch.cuda.set_device(0)
-    dims = (args.lattice,) * 4
+    dims = tuple(int(v) for v in args.dims.split(",")) if args.dims else (args.lattice,) * 4
+    # the numpy generator: the profiling case avoids torch's linear algebra,
+    # whose library a profiler's environment may not load
     lat = Lattice(dims, DOMAIN, -1, "chiral", "cuda:0").setup(random_su3_field(dims, EPS, GAUGE_SEED), KAPPA, CSW)
+    if args.sap_domain:
+        B.qcd_set_sap_domain(lat.ctx, [int(v) for v in args.sap_domain.split(",")])
     b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, SOURCE_SEED))).cuda().contiguous()
     prec = B.PREC_DOUBLE if args.kernel == "dslash64" else B.PREC_SINGLE
     if args.shape is not None:
@@ -345,7 +349,7 @@ def run_kernel_case(args):
     B.qcd_import_spinor(lat.ctx, a, b.expand((nrhs,) + tuple(b.shape)).contiguous() if nrhs > 1 else b, prec, nrhs)
     for _ in range(args.reps):
         if args.kernel.startswith("sap"):
-            sp = B.PREC_HALF if args.kernel == "sap16" else B.PREC_SINGLE
+            sp = {"sap16": B.PREC_HALF, "sap16g": B.PREC_HALF_GAUGE}.get(args.kernel, B.PREC_SINGLE)
             B.qcd_sap_apply_nrhs(lat.ctx, o, a, nrhs, N_SAP, N_JAC, sp, 0)
         else:
             B.qcd_apply_D(lat.ctx, o, a, prec, nrhs=nrhs)
@@ -364,9 +368,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-48", action="store_true", help="skip the 48^4 batched comparison")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged 32-lattice batch comparison")
-    ap.add_argument("--kernel", choices=["sap16", "sap32", "dslash", "dslash64"], default=None,
+    ap.add_argument("--no-n2", action="store_true", help="skip the paper-parameter (16x6x4x3 domains) rates")
+    ap.add_argument("--kernel", choices=["sap16", "sap16g", "sap32", "dslash", "dslash64"], default=None,
                     help="profiling case: set up the workload and run only REPS applications of one kernel")
     ap.add_argument("--lattice", type=int, default=32, help="lattice extent of the profiling case")
+    ap.add_argument("--dims", default=None, help="lattice extents Lx,Ly,Lz,Lt of the profiling case")
+    ap.add_argument("--sap-domain", default=None, help="SAP domain extents of the profiling case (qcd_set_sap_domain)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the profiling case")
     ap.add_argument("--shape", type=int, default=None, help="fix the SAP block-kernel shape of the profiling case")
@@ -621,6 +628,12 @@ def main():
         import bench_configs
         barrier()
         line["north_star_48x4"] = bench_configs.north_star_48x4(reps=1)
+        barrier()
+    if not args.no_n2:
+        # the paper's parameters (n_sap 4, n_jac 2) on its own 16x6x4x3 SAP
+        # domains, per BiCGStab iteration, against Table 2's A64FX node
+        import bench_configs
+        line["paper_parameters_n2"] = bench_configs.n2_paper_domains(float32=False)
         barrier()
     if not args.no_ragged:
         # the ragged batch of 32 lattices (8^4..16^4) in shared launches, against

@@ -346,67 +346,75 @@ def _paper_flop_per_site_iter(domain, n_sap, n_jac, hops=(168, 168, 168, 168)):
     return 2 * (n_sap + 1) * (f_in + n_jac * (f_in + 48) + f_out) + 96 * n_sap + 48 + 1008
 
 
-def n2(args):
-    """The paper's algorithm parameters (n_sap 4, n_jac 2, float32 SAP-BiCGStab):
-    BiCGStab iterations per second from the difference of two fixed-length
-    solves, and the rate in the paper's flop accounting.  Paper, one A64FX
-    node (4 processes): 1.38e7 site-iterations/s, 0.83 TFLOPS (Table 2,
-    first row, 32x6x4x3 per process = two 16x6x4x3 domains).  Measured on
-    32^4 with 4^4 domains (the shared-memory block kernel), and on
-    64x24x32x24 both with the paper's own 16x6x4x3 SAP domains (the
-    general-domain kernel; fields stored in 4^4 blocks) and with 4^4
-    domains."""
+def _n2_rate(lat, dims, prec, flop, flop_paper_basis=None, n_sap=4, n_jac=2):
+    """ms per BiCGStab iteration from the difference of two fixed-length solves
+    (10 and 30 iterations, one outer step, graph loop)."""
     from lattice_inputs import gaussian_spinor
+    from paper_2109_10687_gb300 import binding as B
+    vol = int(np.prod(dims))
+    b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2001))).cuda().contiguous()
+    x = torch.zeros_like(b)
+    times = {}
+    for iters in (10, 30):
+        p = _params(prec, 1e-30, 2)
+        p.n_sap, p.n_jac = n_sap, n_jac
+        p.inner_tol, p.max_inner, p.max_outer = 1e-30, iters, 1
+        B.qcd_solve(lat.ctx, x, b, 1, p, raise_on_error=False)
+        t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, p, raise_on_error=False), 3)
+        times[iters] = (t, info.inner_iters)
+    (t1, i1), (t2, i2) = times[10], times[30]
+    t_iter = (t2 - t1) / max(1, i2 - i1)
+    r = {"lattice": list(dims), "ms_per_iteration": 1e3 * t_iter, "iterations": [i1, i2],
+         "site_iterations_per_s": vol / t_iter, "flop_per_site_iteration": flop,
+         "tflops_paper_accounting": flop * vol / t_iter / 1e12,
+         "vs_a64fx_node_site_iterations": vol / t_iter / 1.38e7}
+    if flop_paper_basis is not None:
+        r["flop_per_site_iteration_paper_basis"] = flop_paper_basis
+        r["tflops_paper_accounting_paper_basis"] = flop_paper_basis * vol / t_iter / 1e12
+    return r
+
+
+def n2_paper_domains(float32=True):
+    """The paper's parameters (n_sap 4, n_jac 2) on 64x24x32x24 with its own
+    16x6x4x3 SAP domains (float16 links and C_inv on the cluster kernel; and
+    float32 on the one-CTA kernel) and with 4^4 domains, against one A64FX
+    node's 1.38e7 site-iterations/s (Table 2, first row)."""
     from paper_2109_10687_gb300 import binding as B
     n_sap, n_jac = 4, 2
     out = {}
-
-    def rate(lat, dims, prec, flop, flop_paper_basis=None):
-        vol = int(np.prod(dims))
-        b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2001))).cuda().contiguous()
-        x = torch.zeros_like(b)
-        times = {}
-        for iters in (10, 30):
-            p = _params(prec, 1e-30, 2)
-            p.n_sap, p.n_jac = n_sap, n_jac
-            p.inner_tol, p.max_inner, p.max_outer = 1e-30, iters, 1
-            B.qcd_solve(lat.ctx, x, b, 1, p, raise_on_error=False)
-            t, (rc, info) = _timed(lambda: B.qcd_solve(lat.ctx, x, b, 1, p, raise_on_error=False), 3)
-            times[iters] = (t, info.inner_iters)
-        (t1, i1), (t2, i2) = times[10], times[30]
-        t_iter = (t2 - t1) / max(1, i2 - i1)
-        r = {"lattice": list(dims), "ms_per_iteration": 1e3 * t_iter, "iterations": [i1, i2],
-             "site_iterations_per_s": vol / t_iter, "flop_per_site_iteration": flop,
-             "tflops_paper_accounting": flop * vol / t_iter / 1e12,
-             "vs_a64fx_node_site_iterations": vol / t_iter / 1.38e7}
-        if flop_paper_basis is not None:
-            r["flop_per_site_iteration_paper_basis"] = flop_paper_basis
-            r["tflops_paper_accounting_paper_basis"] = flop_paper_basis * vol / t_iter / 1e12
-        return r
-
-    # 32^4 on 4^4 domains (the shared-memory block kernel)
-    dims, domain = (32, 32, 32, 32), (4, 4, 4, 4)
-    flop = _paper_flop_per_site_iter(domain, n_sap, n_jac)
-    lat = _lat(dims, 0.3, 0.125, 1.0, 1001, domain)
-    for name, prec in (("float32", "single"), ("float16_storage", "half")):
-        out[name] = rate(lat, dims, prec, flop)
-    lat.close()
-    # 64x24x32x24: the paper's 16x6x4x3 domains, and 4^4 domains on the same lattice
     dims = (64, 24, 32, 24)
     lat = _lat(dims, 0.3, 0.125, 1.0, 1001, (4, 4, 4, 4))
-    out["float32_64x24x32x24_domains_4x4x4x4"] = rate(lat, dims, "single",
-                                                      _paper_flop_per_site_iter((4, 4, 4, 4), n_sap, n_jac))
+    out["float32_domains_4x4x4x4"] = _n2_rate(lat, dims, "single", _paper_flop_per_site_iter((4, 4, 4, 4), n_sap, n_jac))
     paper = (16, 6, 4, 3)
     B.qcd_set_sap_domain(lat.ctx, paper)
     # chiral basis (168 flop for every hop, what the kernels compute) and the
     # paper's basis (156 for a temporal hop), which reproduces Tables 2-3
-    out["float32_64x24x32x24_domains_16x6x4x3"] = rate(
-        lat, dims, "single", _paper_flop_per_site_iter(paper, n_sap, n_jac),
-        _paper_flop_per_site_iter(paper, n_sap, n_jac, hops=(168, 168, 168, 156)))
-    out["float16_gauge_64x24x32x24_domains_16x6x4x3"] = rate(
-        lat, dims, "half_gauge", _paper_flop_per_site_iter(paper, n_sap, n_jac),
-        _paper_flop_per_site_iter(paper, n_sap, n_jac, hops=(168, 168, 168, 156)))
+    fl, fl_paper = (_paper_flop_per_site_iter(paper, n_sap, n_jac),
+                    _paper_flop_per_site_iter(paper, n_sap, n_jac, hops=(168, 168, 168, 156)))
+    out["float16_gauge_domains_16x6x4x3"] = _n2_rate(lat, dims, "half_gauge", fl, fl_paper)
+    if float32:
+        out["float32_domains_16x6x4x3"] = _n2_rate(lat, dims, "single", fl, fl_paper)
+    out["tuning"] = [ln for ln in B.qcd_tuning_report(lat.ctx).splitlines() if ln.startswith("sap_general")]
     lat.close()
+    return out
+
+
+def n2(args):
+    """The paper's algorithm parameters (n_sap 4, n_jac 2): BiCGStab iterations
+    per second and the rate in the paper's flop accounting.  Paper, one A64FX
+    node (4 processes): 1.38e7 site-iterations/s, 0.83 TFLOPS (Table 2, first
+    row, 32x6x4x3 per process = two 16x6x4x3 domains).  Measured on 32^4 with
+    4^4 domains (the shared-memory block kernel), and on 64x24x32x24 with the
+    paper's own 16x6x4x3 domains and with 4^4 domains."""
+    out = {}
+    dims, domain, n_sap, n_jac = (32, 32, 32, 32), (4, 4, 4, 4), 4, 2
+    flop = _paper_flop_per_site_iter(domain, n_sap, n_jac)
+    lat = _lat(dims, 0.3, 0.125, 1.0, 1001, domain)
+    for name, prec in (("float32", "single"), ("float16_storage", "half")):
+        out[name] = _n2_rate(lat, dims, prec, flop)
+    lat.close()
+    for k, v in n2_paper_domains().items():
+        out["64x24x32x24_" + k] = v
     return {"config": {"workload": "eps 0.3, kappa 0.125, c_sw 1.0; SAP-BiCGStab with the paper's n_sap 4, n_jac 2: "
                                    "32^4 on 4^4 domains; 64x24x32x24 on the paper's 16x6x4x3 domains and on 4^4 "
                                    "domains; fixed iteration counts (graph loop)"},
