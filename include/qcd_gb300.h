@@ -333,7 +333,9 @@ int qcd_batch_set_shared(qcd_batch* batch, int enable);
  *   clover leaves; with project = 1 grad_U holds TA(G U^dag) instead, the
  *   su(3) projection (traceless anti-Hermitian part).
  * x and lam may be supplied (non-NULL, canonical float64 device fields) to
- * skip the two solves; otherwise they are solved with params.
+ * skip the two solves; otherwise they are solved with params (when both are
+ * needed and params->outer_restart = 0, as the two right-hand sides b and
+ * gamma_5 eta of one batched solve).
  * grad_U layout: canonical gauge layout. */
 int qcd_grad(qcd_ctx* ctx, const double* eta, const double* b, const double* x,
              const double* lam, double* grad_b, double* grad_U, int project,

@@ -332,6 +332,31 @@ extern "C" int qcd_grad(qcd_ctx* ctx, const double* eta, const double* b, const 
     else qcd_solve_params_default(&P);
     P.x_is_guess = 0;
     qcd_solve_info info;
+    const int pb = ctx->basis == QCD_BASIS_PAPER;
+    if (!x && !lam && P.outer_restart == 0) {
+      // both solves at once: D [x, y] = [b, gamma_5 eta] as two right-hand
+      // sides of one batched solve (every launch serves both), lambda = gamma_5 y
+      double *rhs2 = nullptr, *sol2 = nullptr;
+      QCD_CUDA_CHECK(cudaMalloc(&rhs2, 2 * cbytes));
+      guard.p[4] = rhs2;
+      QCD_CUDA_CHECK(cudaMalloc(&sol2, 2 * cbytes));
+      guard.p[5] = sol2;
+      QCD_CUDA_CHECK(cudaMemcpyAsync(rhs2, b, cbytes, cudaMemcpyDeviceToDevice, st));
+      QCD_CUDA_CHECK(cudaMemcpyAsync(rhs2 + (size_t)g.vol * 24, eta, cbytes, cudaMemcpyDeviceToDevice, st));
+      gamma5_canonical_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g.vol, rhs2 + (size_t)g.vol * 24, pb);
+      check_launch();
+      ctx->launches++;
+      const int rc = qcd_solve(ctx, sol2, rhs2, 2, 1, &P, &info, stream);
+      if (rc != QCD_OK) throw Error{rc, "qcd_grad: solve failed: " + ctx->err};
+      QCD_CUDA_CHECK(cudaMemcpyAsync(xs, sol2, cbytes, cudaMemcpyDeviceToDevice, st));
+      QCD_CUDA_CHECK(cudaMemcpyAsync(ls, sol2 + (size_t)g.vol * 24, cbytes, cudaMemcpyDeviceToDevice, st));
+      gamma5_canonical_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g.vol, ls, pb);
+      check_launch();
+      ctx->launches++;
+      cudaFree(rhs2);
+      cudaFree(sol2);
+      guard.p[4] = guard.p[5] = nullptr;
+    } else {
     if (x) {
       QCD_CUDA_CHECK(cudaMemcpyAsync(xs, x, cbytes, cudaMemcpyDeviceToDevice, st));
     } else {
@@ -345,7 +370,6 @@ extern "C" int qcd_grad(qcd_ctx* ctx, const double* eta, const double* b, const 
       QCD_CUDA_CHECK(cudaMalloc(&e5, cbytes));
       guard.p[4] = e5;
       QCD_CUDA_CHECK(cudaMemcpyAsync(e5, eta, cbytes, cudaMemcpyDeviceToDevice, st));
-      const int pb = ctx->basis == QCD_BASIS_PAPER;
       gamma5_canonical_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g.vol, e5, pb);
       check_launch();
       ctx->launches++;
@@ -354,6 +378,7 @@ extern "C" int qcd_grad(qcd_ctx* ctx, const double* eta, const double* b, const 
       gamma5_canonical_kernel<<<grid_for(g.vol, 256), 256, 0, st>>>(g.vol, ls, pb);
       check_launch();
       ctx->launches++;
+    }
     }
     if (grad_b) QCD_CUDA_CHECK(cudaMemcpyAsync(grad_b, ls, cbytes, cudaMemcpyDeviceToDevice, st));
     if (grad_U) {
