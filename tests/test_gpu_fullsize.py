@@ -123,3 +123,80 @@ def test_solve_64x4_sampled():
         assert np.sqrt(num / den) < 1e-8
     finally:
         lat.close()
+
+
+def test_ragged_batch_32_lattices_as_benchmarked():
+    """The ragged batch the benchmark times (32 lattices with extents drawn
+    from {8, 16}, kappa ~ U[0.115, 0.125], the same seeds), solved in shared
+    launches: every lattice's residual b - D x recomputed by the site-by-site
+    float64 oracle on 16 sampled sites, against 1e-9 of |b| there."""
+    from lattice_inputs import random_su3_field
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300.lattice import Lattice
+    rng = np.random.default_rng(5000)
+    lats, us, bs, kappas = [], [], [], []
+    try:
+        for i in range(32):
+            dims = tuple(int(v) for v in rng.choice([8, 16], size=4))
+            kappa = float(rng.uniform(0.115, 0.125))
+            u = random_su3_field(dims, 0.3, 5000 + i)
+            lats.append(Lattice(dims, (4, 4, 4, 4), -1, "chiral").setup(u, kappa, 1.0))
+            us.append(u)
+            kappas.append(kappa)
+            bs.append(gaussian_spinor(dims, 7000 + i))
+        bt = B.qcd_batch_create([l.ctx for l in lats])
+        try:
+            bd = [torch.view_as_real(torch.from_numpy(b)).cuda().contiguous() for b in bs]
+            xd = [torch.zeros_like(b) for b in bd]
+            rc, infos = B.qcd_batch_solve(bt, xd, bd, _params())
+            assert rc == 0 and all(i.true_resid < 1e-10 for i in infos)
+        finally:
+            B.qcd_batch_destroy(bt)
+        g = gamma_chiral()
+        srng = np.random.default_rng(17)
+        for i, (lat, u, b, x) in enumerate(zip(lats, us, bs, xd)):
+            xn = to_np(torch.view_as_complex(x))
+            num = den = 0.0
+            for _ in range(16):
+                c = tuple(int(srng.integers(0, lat.dims[mu])) for mu in range(4))
+                r = b[c[3], c[2], c[1], c[0]] - pointwise.D_at(u, xn, c, kappas[i], 1.0, g, -1)
+                num += np.sum(np.abs(r) ** 2)
+                den += np.sum(np.abs(b[c[3], c[2], c[1], c[0]]) ** 2)
+            assert np.sqrt(num / den) < 1e-9, (i, np.sqrt(num / den))
+    finally:
+        for l in lats:
+            l.close()
+
+
+@pytest.mark.parametrize("sap_prec,shape", [("half_gauge", 0), ("single", 1)])
+def test_paper_domains_full_size(sap_prec, shape):
+    """The paper-parameter workload of the benchmark line at full size:
+    64x24x32x24 on the paper's 16x6x4x3 SAP domains (the cluster kernel with
+    float16 links and C_inv; the one-CTA kernel in float32), n_sap 4, n_jac 2,
+    solved to 1e-10; the residual recomputed by the site-by-site float64
+    oracle on 48 sampled sites."""
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300.lattice import Lattice
+    dims = (64, 24, 32, 24)
+    kappa, csw = 0.125, 1.0
+    u = random_su3_field_fast(dims, 0.3, 1001)
+    lat = Lattice(dims, (4, 4, 4, 4), -1, "chiral").setup(u, kappa, csw)
+    try:
+        B.qcd_set_sap_domain(lat.ctx, (16, 6, 4, 3))
+        B.qcd_set_sap_shape(lat.ctx, shape)
+        b = gaussian_spinor(dims, 2001)
+        x, rc, info = lat.solve(b, tol=1e-10, inner_tol=1e-6 if sap_prec == "single" else 1e-5, n_sap=4, n_jac=2,
+                                sap_prec=sap_prec, use_graph=2, max_inner=2000)
+        assert rc == 0 and info.true_resid < 1e-10
+        x = to_np(x)
+        g = gamma_chiral()
+        rng = np.random.default_rng(19)
+        num = den = 0.0
+        for _ in range(48):
+            c = tuple(int(rng.integers(0, dims[mu])) for mu in range(4))
+            r = b[c[3], c[2], c[1], c[0]] - pointwise.D_at(u, x, c, kappa, csw, g, -1)
+            num += np.sum(np.abs(r) ** 2)
+            den += np.sum(np.abs(b[c[3], c[2], c[1], c[0]]) ** 2)
+        assert np.sqrt(num / den) < 1e-8
+    finally:
+        lat.close()
