@@ -193,3 +193,23 @@ def test_batch_solve_follows_a_new_kappa(batch):
     finally:
         B.qcd_set_params(p0.lat.ctx, old_kappa, p0.csw)
         B.qcd_build_clover(p0.lat.ctx)
+
+
+def test_batch_solve_periodic_time_and_paper_basis():
+    """The shared-launch solve with periodic time (bc_t = +1) and with fields in
+    the paper's gamma basis (rotated on import and export per lattice): every
+    lattice's oracle residual below 1e-10."""
+    from paper_2109_10687_gb300 import binding as B
+    for bc_t, basis in ((+1, "chiral"), (-1, "paper")):
+        probs = [Problem(d, (4, 4, 4, 4), eps=0.3, kappa=k, csw=1.0, seed=s + 50, bc_t=bc_t, basis=basis)
+                 for d, k, s in LATTICES[:3]]
+        bt = B.qcd_batch_create([p.lat.ctx for p in probs])
+        try:
+            rc, infos, xs, bs = _solve_batch(bt, probs, 6800, sap_prec=B.PREC_HALF)
+            assert rc == 0
+            for p, x, b in zip(probs, xs, bs):
+                assert _oracle_resid(p, x, b) < 1e-10, (bc_t, basis)
+        finally:
+            B.qcd_batch_destroy(bt)
+            for p in probs:
+                p.close()

@@ -314,3 +314,28 @@ def test_cluster_sap_wait_timeout_is_reported_and_context_survives():
         assert rel_l2(got, sap.msap(op, b, 1, 2)) <= 5e-3
     finally:
         p.close()
+
+
+def test_cluster_sap_kernel_periodic_time():
+    """The cluster kernel with periodic time (bc_t = +1; the boundary sign
+    sits on the surface hops across t = Lt - 1 <-> 0): bit for bit equal to the
+    one-CTA kernel and within 1e-5 of the oracle on the rounded operator."""
+    import copy
+    from paper_2109_10687_gb300 import binding as B
+    from oracle.dirac import CloverWilson
+    p = Problem((32, 12, 8, 6), (4, 2, 2, 1), eps=0.3, kappa=0.12, csw=1.0, seed=1153, bc_t=+1, oracle=False)
+    try:
+        B.qcd_set_sap_domain(p.lat.ctx, (16, 6, 4, 3))
+        op = CloverWilson(p.u, 0.12, 1.0, p.gammas, bc_t=+1, domain=(16, 6, 4, 3))
+        op16 = copy.copy(op)
+        op16.u = _half_round(op.u)
+        op16.cinv = _half_round(op.cinv)
+        b = p.source(2162)
+        out = {}
+        for shape in (0, 1):
+            B.qcd_set_sap_shape(p.lat.ctx, shape)
+            out[shape] = to_np(p.lat.sap(b, 2, 2, "half_gauge"))
+        assert np.array_equal(out[0], out[1])
+        assert rel_l2(out[0], sap.msap(op16, b, 2, 2)) <= 1e-5
+    finally:
+        p.close()
