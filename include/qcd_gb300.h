@@ -374,8 +374,11 @@ int qcd_set_tuning(qcd_ctx* ctx, int enable);
 
 /* Fix the SAP kernel's shape: -1 autotuned (default).  For 4^4 domains:
  * 0 one site per thread (256 threads per domain), 1 two sites per thread
- * (128 threads per domain, each thread two independent site streams); every
- * shape computes the same M_SAP bit for bit.  For domains set with
+ * (128 threads per domain, each thread two independent site streams), 2 one
+ * site per thread and one CTA per domain and right-hand side (with nrhs > 1;
+ * each CTA stages the domain's links and C_inv itself, instead of running
+ * every right-hand side through one staged copy); every shape computes the
+ * same M_SAP bit for bit.  For domains set with
  * qcd_set_sap_domain and float16 links and C_inv (QCD_PREC_HALF_GAUGE):
  * 0 one thread-block cluster per domain, one CTA per time slice (at most 8
  * slices of at most 448 sites), links and C_inv staged in shared memory and

@@ -36,7 +36,8 @@
 // Shared memory: f16 103 KB (two CTAs per SM), f32 176 KB (one CTA per SM).
 // Three mbarriers: the staged links and the staged C_inv (once each; the
 // surface term needs only the links, so it starts before C_inv has landed)
-// and the halo copy (once per right-hand side, parity r & 1).
+// and the halo copy (once per right-hand side of the CTA, parity i & 1 for
+// its i-th).
 
 #include <cstdio>
 #include <cstring>
@@ -517,10 +518,14 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
   // the staged links and C_inv are constant during a solve; everything read
   // below may come from the previous launch, which must be complete
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  for (int r = 0; r < a.nrhs; ++r) {
+  // right-hand sides of this CTA: all of them, or (grid y > 1) the one of blockIdx.y
+  const int r_begin = gridDim.y > 1 ? (int)blockIdx.y : 0;
+  const int r_end = gridDim.y > 1 ? r_begin + 1 : a.nrhs;
+  for (int r = r_begin; r < r_end; ++r) {
+    const int i = r - r_begin;  // this CTA's i-th right-hand side
     const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
     const int rhs_off = r * g.ndom;
-    if (r > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
+    if (i > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
     if (a.do_surface && tid == 0) {
       // the halo lands in the slots (the start of the x buffer); order the
       // earlier generic accesses to it before the asynchronous copy
@@ -534,13 +539,13 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
       if (a.s_in32.p) a.s_in32.load(g, domr, tid + j * NT, src[j]);
       else a.s_in.load(g, domr, tid + j * NT, src[j]);
     }
-    if (r == 0) __syncthreads();  // barrier initialisation visible to every thread
+    if (i == 0) __syncthreads();  // barrier initialisation visible to every thread
     {
-      const bool ok_l = r > 0 || mbar_wait_bounded(lbar, 0);
-      const bool ok_h = !a.do_surface || mbar_wait_bounded(hbar, r & 1);
+      const bool ok_l = i > 0 || mbar_wait_bounded(lbar, 0);
+      const bool ok_h = !a.do_surface || mbar_wait_bounded(hbar, i & 1);
       if (__syncthreads_or(!(ok_l && ok_h))) {
-        st_give_up(a.status, tid, !ok_l, lbar, 0, !ok_h, hbar, r & 1);
-        if (r == 0) mbar_wait_bounded(cbar, 0);
+        st_give_up(a.status, tid, !ok_l, lbar, 0, !ok_h, hbar, i & 1);
+        if (i == 0) mbar_wait_bounded(cbar, 0);
         return;
       }
     }
@@ -556,7 +561,7 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
       }
       __syncthreads();  // every thread has taken its face slots before x overwrites them
     }
-    if (r == 0) {
+    if (i == 0) {
       // C_inv is first needed here
       const bool ok_c = mbar_wait_bounded(cbar, 0);
       if (__syncthreads_or(!ok_c)) {
@@ -753,7 +758,8 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
 // if it is set, else to x.  halo holds 96 bytes per site and right-hand side.
 template <bool HALF, typename SIO, int SPT>
 static void staged_sequence_shape(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b,
-                                  F32Spinor x_out32, float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st) {
+                                  F32Spinor x_out32, float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st,
+                                  bool rhs_grid = false) {
   StagedArgs<HALF, SIO> a;
   a.g = ctx->geom;
   a.nrhs = nrhs;
@@ -784,7 +790,7 @@ static void staged_sequence_shape(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, S
       a.do_halo = (last && colour == 1) ? 0 : 1;
       LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(ctx->geom.nhalf);
+      cfg.gridDim = dim3(ctx->geom.nhalf, rhs_grid ? nrhs : 1);
       cfg.blockDim = dim3(ST_THREADS / SPT);
       cfg.dynamicSmemBytes = st_smem_bytes<HALF>();
       cfg.stream = st;
@@ -799,12 +805,16 @@ static void staged_sequence_shape(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, S
   }
 }
 
-// The block-kernel shape (sites per thread) is chosen by the autotuner on
-// the first M_SAP of each precision, lattice, right-hand-side count and
-// n_jac: it times the whole sequence in every shape on the caller's
-// buffers (M_SAP is a function of its input alone, so the repeated runs
-// leave the same result) and keeps the faster.  qcd_set_sap_shape fixes it.
-static const char* const kSapShapes[] = {"256x1site", "128x2sites"};
+// The block-kernel shape is chosen by the autotuner on the first M_SAP of
+// each precision, lattice, right-hand-side count and n_jac: it times the
+// whole sequence in every shape on the caller's buffers (M_SAP is a function
+// of its input alone, so the repeated runs leave the same result) and keeps
+// the fastest.  Shapes: one or two sites per thread, and, with several
+// right-hand sides, one CTA per domain and right-hand side (each stages the
+// domain's links and C_inv for itself; more CTAs where a lattice has too few
+// domains to fill the GPU) instead of one CTA running all of them through
+// its staged operator.  qcd_set_sap_shape fixes the shape.
+static const char* const kSapShapes[] = {"256x1site", "128x2sites", "256x1site_rhs_grid"};
 
 template <bool HALF, typename SIO>
 static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b, F32Spinor x_out32,
@@ -813,7 +823,8 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
     if (v == 1)
       staged_sequence_shape<HALF, SIO, 2>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st);
     else
-      staged_sequence_shape<HALF, SIO, 1>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st);
+      staged_sequence_shape<HALF, SIO, 1>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st,
+                                          v == 2 && nrhs > 1);
   };
   int v = ctx->sap_shape;
   if (v < 0) {
@@ -822,7 +833,7 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
     std::snprintf(key, sizeof key, "sap_staged_%s L%dx%dx%dx%d nrhs%d n_sap%d n_jac%d",
                   HALF ? (std::is_same<SIO, F16Spinor>::value ? "f16" : "f16gauge") : "f32", g.L[0], g.L[1], g.L[2],
                   g.L[3], nrhs, n_sap, n_jac);
-    v = tune_pick(ctx, key, 2, kSapShapes, run, st);
+    v = tune_pick(ctx, key, nrhs > 1 ? 3 : 2, kSapShapes, run, st);
   }
   run(v);
 }

@@ -100,37 +100,42 @@ def test_msap_multi_rhs_matches_single_rhs(wide, sap_prec, with_A):
 
 @pytest.mark.parametrize("sap_prec", ["single", "half_gauge", "half"])
 def test_sap_kernel_shapes_agree_bit_for_bit(wide, sap_prec):
-    """The two shapes of the SAP block kernel for 4^4 domains (one site per
-    thread, two sites per thread) do the same arithmetic per site, so their
-    M_SAP agree bit for bit, single and batched; both match the oracle's
-    literal Algorithm 1 within the storage's tolerance.  With the shape left
-    to the autotuner, the tuning report lists the SAP key and both shapes."""
+    """The shapes of the SAP block kernel for 4^4 domains (one site per
+    thread, two sites per thread, one CTA per domain and right-hand side) do
+    the same arithmetic per site, so their M_SAP agree bit for bit, single and
+    batched; all match the oracle's literal Algorithm 1 within the storage's
+    tolerance.  With the shape left to the autotuner, the tuning report lists
+    the SAP key and the shapes."""
     from paper_2109_10687_gb300 import binding as B
     ctx = wide.lat.ctx
     b = wide.source(2120)
     srcs = np.stack([wide.source(2121 + r) for r in range(2)])
     out = {}
     try:
-        for shape in (0, 1):
+        for shape in (0, 1, 2):
             B.qcd_set_sap_shape(ctx, shape)
             out[shape] = (to_np(wide.lat.sap(b, 4, 4, sap_prec)), to_np(wide.lat.sap(srcs, 4, 4, sap_prec, nrhs=2)))
         B.qcd_set_sap_shape(ctx, -1)
         tuned = to_np(wide.lat.sap(b, 4, 4, sap_prec))
+        tuned2 = to_np(wide.lat.sap(srcs, 4, 4, sap_prec, nrhs=2))
     finally:
         B.qcd_set_sap_shape(ctx, -1)
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    for shape in (1, 2):
+        assert np.array_equal(out[0][0], out[shape][0])
+        assert np.array_equal(out[0][1], out[shape][1])
+    assert np.array_equal(tuned2, out[0][1])
     assert np.array_equal(tuned, out[0][0])
     tol = 1e-5 if sap_prec == "single" else 5e-3
     assert rel_l2(out[1][0], sap.msap(wide.op, b, 4, 4)) <= tol
     rep = B.qcd_tuning_report(ctx)
     line = [ln for ln in rep.splitlines() if ln.startswith("sap_staged_")]
     assert line and "256x1site" in line[0] and "128x2sites" in line[0]
+    assert any("nrhs2" in ln and "256x1site_rhs_grid" in ln for ln in line)
 
 
 def test_sap_shape_rejects_unknown_value(wide):
     from paper_2109_10687_gb300 import binding as B
-    assert B.lib().qcd_set_sap_shape(wide.lat.ctx, 2) == B.QCD_ERR_ARG
+    assert B.lib().qcd_set_sap_shape(wide.lat.ctx, 3) == B.QCD_ERR_ARG
     assert B.lib().qcd_set_sap_shape(wide.lat.ctx, -2) == B.QCD_ERR_ARG
 
 

@@ -88,7 +88,7 @@ def test_double_float_residual_bound(kappa, seed):
         p.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, -1])
+@pytest.mark.parametrize("shape", [0, 1, 2, -1])
 def test_solve_with_each_sap_kernel_shape(c1, c1_ref, shape):
     """The solve with each shape of the SAP block kernel (one or two sites
     per thread, or the autotuned one) reaches the float64 true residual 1e-10
