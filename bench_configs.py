@@ -176,6 +176,7 @@ def north_star_48x4(reps=1, f32_vectors=False):
     out["faster_than_plain_f32"] = bool(t_batch < out["sequential_plain_f32"]["s"])
     out["setup_s"] = t_setup
     out["clocks"] = clk.stop()
+    out["tuning"] = [ln for ln in B.qcd_tuning_report(lat.ctx).splitlines() if ln.startswith("sap_staged")]
     lat.close()
     return out
 
