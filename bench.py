@@ -377,7 +377,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the profiling case")
     ap.add_argument("--shape", type=int, default=None, help="fix the SAP block-kernel shape of the profiling case")
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5ragged", "n2"],
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5ragged", "n2", "cpu"],
                     help="c2 (default) is the benchmark line; the others measure the other workloads")
     args = ap.parse_args()
     if args.config != "c2":

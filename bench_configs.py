@@ -20,6 +20,7 @@ seeded and synthetic.
 """
 
 import json
+import os
 import time
 
 import numpy as np
@@ -423,9 +424,101 @@ def n2(args):
             "unit": "site-iterations/s", "results": out}
 
 
+def _oracle_cpu_task(job):
+    """One single-threaded oracle timing job (runs in a spawned worker):
+    ("D", dims) times one float64 D apply, ("iter", dims) one SAP-BiCGStab
+    iteration (two A M_SAP applications, n_sap 4, n_jac 4, 4^4 domains),
+    both after building the operator outside the clock."""
+    from lattice_inputs import gaussian_spinor, random_su3_field
+    from oracle import sap
+    from oracle.dirac import CloverWilson
+    from oracle.gamma import gamma_chiral
+    if job is None:
+        return None
+    kind, dims = job
+    op = CloverWilson(random_su3_field(dims, 0.3, 1001), 0.125, 1.0, gamma_chiral(), bc_t=-1, domain=(4, 4, 4, 4))
+    x = gaussian_spinor(dims, 2001)
+    if kind == "D":
+        op.D(x)
+        t0 = time.perf_counter()
+        op.D(x)
+        return time.perf_counter() - t0
+    t0 = time.perf_counter()
+    y = sap.am_sap(op, x, 4, 4)
+    sap.am_sap(op, y, 4, 4)
+    return time.perf_counter() - t0
+
+
+def _oracle_pool(jobs, procs):
+    """Run oracle timing jobs on `procs` single-threaded spawned workers;
+    returns (wall seconds, per-job results)."""
+    import multiprocessing as mp
+    import bench as bn
+    saved = {k: os.environ.get(k) for k in bn._ONE_THREAD_ENV}
+    for k in bn._ONE_THREAD_ENV:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            pool.map(_oracle_cpu_task, [None] * procs, chunksize=1)
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_cpu_task, jobs, chunksize=1)
+            return time.perf_counter() - t0, res
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def cpu(args):
+    """The float64 oracle timed on the host cores, each worker process one
+    thread (numpy's elementwise work is single-threaded, so all cores means
+    one independent job per core):
+    - D apply at 8^4, 16^4 and 32^4 on one thread, and one 16^4 apply per
+      core at once; bytes counted as the float32 D's 768 B per site doubled
+      for float64 (1536 B), 1824 flop per site;
+    - the 8^4 solve of the main benchmark's recipe (Algorithm 4 around
+      Algorithm 5 to 1e-10) on one thread and one per core at once;
+    - one SAP-BiCGStab iteration at 16^4 on one thread.  Solves at 16^4 and
+      above take the oracle tens of minutes (an A M_SAP application costs
+      about 20 s at 16^4), so their per-iteration times at 32^4, 48^4 and
+      64^4 are extrapolated by volume from the 16^4 figure and labelled so."""
+    import bench as bn
+    cores = bn.host_cores()
+    out = {"host_cores": cores, "threads_per_process": 1}
+    apply = {}
+    for L in (8, 16, 32):
+        _, (t,) = _oracle_pool([("D", (L,) * 4)], 1)
+        v = L ** 4
+        apply[f"{L}^4_one_thread"] = {"s": t, "gsites_per_s": v / t / 1e9, "gbs": 1536 * v / t / 1e9,
+                                      "gflops": 1824 * v / t / 1e9}
+    _, ts = _oracle_pool([("D", (16,) * 4)] * cores, cores)
+    v = 16 ** 4
+    agg = sum(v / t for t in ts)
+    apply["16^4_all_cores"] = {"processes": cores, "gsites_per_s": agg / 1e9, "gbs": 1536 * agg / 1e9,
+                               "gflops": 1824 * agg / 1e9}
+    out["D_apply_f64"] = apply
+    wall1, (rec,) = bn.oracle_solves(1, 1, 0, bn.ORACLE_DIMS)
+    wallc, recs = bn.oracle_solves(cores, cores, 0, bn.ORACLE_DIMS)
+    out["solve_8^4_to_1e-10"] = {"one_thread_s": wall1, "inner": rec["inner"], "outer": rec["outer"],
+                                 "true_resid": rec["true_resid"], "all_cores_solves_per_s": cores / wallc,
+                                 "all_converged": all(r["converged"] for r in recs + [rec])}
+    _, (ti,) = _oracle_pool([("iter", (16,) * 4)], 1)
+    per_site = ti / 16 ** 4
+    out["sap_bicgstab_iteration_one_thread"] = {
+        "16^4_s": ti,
+        "extrapolated_by_volume_s": {f"{L}^4": per_site * L ** 4 for L in (32, 48, 64)}}
+    return {"config": {"workload": "float64 oracle (numpy) on the host cores: D apply at 8^4, 16^4, 32^4; "
+                                   "8^4 solves to 1e-10; one SAP-BiCGStab iteration at 16^4 "
+                                   "(eps 0.3, kappa 0.125, c_sw 1.0, n_sap 4, n_jac 4, 4^4 domains)"},
+            "metric": "oracle rates", "unit": "mixed (see keys)", "results": out}
+
+
 def run(args):
-    torch.cuda.set_device(0)
-    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "c5ragged": c5ragged, "n2": n2}[args.config]
+    if args.config != "cpu":
+        torch.cuda.set_device(0)
+    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "c5ragged": c5ragged, "n2": n2, "cpu": cpu}[args.config]
     line = fn(args)
     line["name"] = args.config
     print(json.dumps(line))

@@ -96,3 +96,16 @@ def test_sap_byte_model_matches_the_profiled_launch():
     assert bench.sap_bytes_per_launch("half", 0, 0) == 96 + 288 + 96 + 148
     assert bench.sap_bytes_per_launch("half", bench.N_SAP, 1) == 52 + 288 + 96 + 96
     assert abs(bench.sap_bytes_per_site("half") - 659.2) < 1e-9
+
+
+def test_cpu_config_oracle_jobs():
+    """The host-core oracle timing jobs of the CPU configuration: a D apply
+    and one SAP-BiCGStab iteration at 8^4, each timed in a spawned
+    single-threaded worker, return positive seconds; the thread variables
+    are restored afterwards."""
+    sys.path.insert(0, ROOT)
+    import bench_configs
+    before = os.environ.get("OMP_NUM_THREADS")
+    wall, (t_d, t_it) = bench_configs._oracle_pool([("D", (8, 8, 8, 8)), ("iter", (8, 8, 8, 8))], 1)
+    assert 0 < t_d < t_it <= wall
+    assert os.environ.get("OMP_NUM_THREADS") == before
