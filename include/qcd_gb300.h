@@ -377,13 +377,18 @@ int qcd_set_tuning(qcd_ctx* ctx, int enable);
  * (128 threads per domain, each thread two independent site streams), 2 one
  * site per thread and one CTA per domain and right-hand side (with nrhs > 1;
  * each CTA stages the domain's links and C_inv itself, instead of running
- * every right-hand side through one staged copy); every shape computes the
- * same M_SAP bit for bit.  For domains set with
- * qcd_set_sap_domain and float16 links and C_inv (QCD_PREC_HALF_GAUGE):
- * 0 one thread-block cluster per domain, one CTA per time slice (at most 8
- * slices of at most 448 sites), links and C_inv staged in shared memory and
- * the time hops between slices through distributed shared memory; 1 one CTA
- * per domain reading links and C_inv through L1.  QCD_ERR_ARG otherwise. */
+ * every right-hand side through one staged copy), 3 the whole M_SAP
+ * (Algorithm 1, all 2 (n_sap + 1) half-sweeps) in one launch of resident
+ * CTAs that take (half-sweep, domain) items in order and wait, bounded, for
+ * the eight neighbouring domains of the previous half-sweep through
+ * per-domain flags instead of for a whole grid, 4 as 3 with half of the
+ * CTAs starting 10 us later; every shape computes the same M_SAP bit for
+ * bit.  For domains set with qcd_set_sap_domain and float16 links and C_inv
+ * (QCD_PREC_HALF_GAUGE): 0 one thread-block cluster per domain, one CTA per
+ * time slice (at most 8 slices of at most 448 sites), links and C_inv staged
+ * in shared memory and the time hops between slices through distributed
+ * shared memory; 1 to 4 one CTA per domain reading links and C_inv through
+ * L1.  QCD_ERR_ARG for other values. */
 int qcd_set_sap_shape(qcd_ctx* ctx, int shape);
 
 /* Autotuner over SAP domain shapes, by time to solution.  The domain shape

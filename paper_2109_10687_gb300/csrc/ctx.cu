@@ -383,7 +383,7 @@ extern "C" int qcd_destroy(qcd_ctx* ctx) {
   void* ptrs[] = {ctx->d_nbr, ctx->d_lex2dom, ctx->d_tflag, ctx->u64, ctx->u32, ctx->u16, ctx->clov64,
                   ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status,
                   ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32, ctx->udf, ctx->clovdf,
-                  ctx->cl_link, ctx->cl_clov};
+                  ctx->cl_link, ctx->cl_clov, ctx->flow_state};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);

@@ -668,8 +668,9 @@ struct qcd_ctx {
   void* st_link32 = nullptr;
   void* st_clov16 = nullptr;
   void* st_clov32 = nullptr;
+  int* flow_state = nullptr;       // one-launch M_SAP: 2 counters, then one flag per domain (zero at rest)
   bool force_generic_sap = false;  // testing: use the generic SAP kernel
-  int sap_shape = -1;              // SAP block-kernel shape: -1 autotuned, 0 one site, 1 two sites per thread
+  int sap_shape = -1;              // SAP block-kernel shape: -1 autotuned, else an index of the shapes
   bool sap_general = false;        // SAP on domains sap_dom, independent of the storage blocking
   int sap_dom[4] = {0, 0, 0, 0};
   int clover_gen = 0;              // counts clover builds (staging copies follow it)

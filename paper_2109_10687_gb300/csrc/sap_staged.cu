@@ -33,11 +33,14 @@
 //   (these site strides make each warp's reads free of shared-memory bank
 //   conflicts)
 //
+// sap_flow_kernel runs the same half-sweeps, a whole M_SAP, in one launch of
+// resident CTAs ordered by per-domain flags (an autotuner shape).
+//
 // Shared memory: f16 103 KB (two CTAs per SM), f32 176 KB (one CTA per SM).
-// Three mbarriers: the staged links and the staged C_inv (once each; the
-// surface term needs only the links, so it starts before C_inv has landed)
-// and the halo copy (once per right-hand side of the CTA, parity i & 1 for
-// its i-th).
+// Three mbarriers: the staged links and the staged C_inv (once per item a
+// CTA runs; the surface term needs only the links, so it starts before
+// C_inv has landed) and the halo copy (once per right-hand side of an item
+// with a surface term; its phase counts those copies).
 
 #include <cstdio>
 #include <cstring>
@@ -481,14 +484,60 @@ __device__ __forceinline__ void st_give_up(int* status, int tid, bool wait0, uin
   if (wait1) mbar_wait_bounded(bar1, par1);
 }
 
+// What one half-sweep does besides its colour: whether it has a surface term
+// (all but the very first), whether it ends with the residual update (all
+// but the last sweep), whether it is the first sweep (its input is the
+// float32 source s_in32, if that is set) or the last one (the iterate goes
+// to x_out32 or x), and whether it writes the neighbours' halo (all but the
+// very last).
+struct ItemMode {
+  int colour, do_surface, do_update, first, last, do_halo;
+};
+
+template <bool HALF, typename SIO>
+__device__ __forceinline__ ItemMode launch_mode(const StagedArgs<HALF, SIO>& a) {
+  return ItemMode{a.colour, a.do_surface, a.do_update, 1, 1, a.do_halo};
+}
+
+// Thread 0: initialise the three mbarriers (the CTA's first item only) and
+// issue the bulk copies of the domain's links and C_inv.  Before a later
+// item's copies overwrite them, the earlier item's generic reads of the
+// buffers (ordered by a CTA barrier) are ordered before the async writes.
+template <bool HALF, typename SIO>
+__device__ __forceinline__ void st_issue_staging(const StagedArgs<HALF, SIO>& a, int dom, int use,
+                                                 unsigned char* sl, unsigned char* sc, uint64_t* lbar,
+                                                 uint64_t* cbar, uint64_t* hbar) {
+  using ST = StageT<HALF>;
+  if (use == 0) {
+    mbar_init(lbar, 1);
+    mbar_init(cbar, 1);
+    mbar_init(hbar, 1);
+  } else {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  mbar_expect_tx(lbar, ST::LINK_BYTES + a.extra_tx);
+  bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, lbar);
+  mbar_expect_tx(cbar, ST::CLOV_BYTES);
+  bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, cbar);
+}
+
+// One half-sweep of one domain (all of the CTA's right-hand sides).
 // HALF: float16 links and C_inv (two CTAs per SM); SIO: storage of s and x.
 // SPT: sites per thread.  With SPT = 1 a CTA has 256 threads, one per site;
 // with SPT = 2 it has 128 threads, thread tau holding sites tau and
 // tau + 128 (the same x, y, z, t and t + 2), which gives each thread two
 // independent streams of the same arithmetic.  The arithmetic per site is
 // the same in both; the autotuner picks the faster shape.
+// use: how many items this CTA ran before (the staging barriers' phase);
+// hcount: halo copies this CTA issued before (the halo barrier's phase),
+// advanced here; issue: thread 0 issues the staging copies here (else the
+// caller did); pdl_wait: wait for the previous grid before reading its
+// outputs; flow: the halo was written by other CTAs of this grid (ordered
+// by flags), so order those generic writes before the async-proxy copy.
+// Returns false if a wait gave up (status set, copies drained).
 template <bool HALF, typename SIO, int SPT>
-__device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, int blk) {
+__device__ __forceinline__ bool sap_staged_item(const StagedArgs<HALF, SIO>& a, const ItemMode& m, int blk, int use,
+                                                int& hcount, bool issue, bool pdl_wait, bool flow) {
   constexpr int NT = ST_THREADS / SPT;
   extern __shared__ __align__(128) unsigned char smem[];
   using ST = StageT<HALF>;
@@ -499,25 +548,14 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
   uint64_t* cbar = lbar + 1;                                          // staged C_inv
   uint64_t* hbar = lbar + 2;                                          // halo copy
   const Geom& g = a.g;
-  if (loop_idle(g) || (a.skip && *(volatile const int*)a.skip)) return;
   const int tid = threadIdx.x;
-  const int dom = a.colour * g.nhalf + blk;
+  const int dom = m.colour * g.nhalf + blk;
+  const unsigned spar = use & 1;
 
-  // programmatic dependent launch: the next launch in the stream may start
-  // its CTAs while this grid drains
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if (tid == 0) {
-    mbar_init(lbar, 1);
-    mbar_init(cbar, 1);
-    mbar_init(hbar, 1);
-    mbar_expect_tx(lbar, ST::LINK_BYTES + a.extra_tx);
-    bulk_copy_g2s(sl, a.links + (size_t)dom * ST::LINK_BYTES, ST::LINK_BYTES, lbar);
-    mbar_expect_tx(cbar, ST::CLOV_BYTES);
-    bulk_copy_g2s(sc, a.clov + (size_t)dom * ST::CLOV_BYTES, ST::CLOV_BYTES, cbar);
-  }
+  if (issue && tid == 0) st_issue_staging(a, dom, use, sl, sc, lbar, cbar, hbar);
   // the staged links and C_inv are constant during a solve; everything read
   // below may come from the previous launch, which must be complete
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (pdl_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
   // right-hand sides of this CTA: all of them, or (grid y > 1) the one of blockIdx.y
   const int r_begin = gridDim.y > 1 ? (int)blockIdx.y : 0;
   const int r_end = gridDim.y > 1 ? r_begin + 1 : a.nrhs;
@@ -525,32 +563,35 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
     const int i = r - r_begin;  // this CTA's i-th right-hand side
     const int domr = dom + r * g.ndom;  // this right-hand side's copy of the domain
     const int rhs_off = r * g.ndom;
+    const unsigned hpar = hcount & 1;
     if (i > 0) __syncthreads();  // every thread is done with the previous rhs's x in shared memory
-    if (a.do_surface && tid == 0) {
+    if (m.do_surface && tid == 0) {
       // the halo lands in the slots (the start of the x buffer); order the
       // earlier generic accesses to it before the asynchronous copy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (flow) asm volatile("fence.proxy.async.global;" ::: "memory");
       mbar_expect_tx(hbar, HALO_BYTES + a.extra_htx);
       bulk_copy_g2s(sx, a.halo + (size_t)domr * HALO_F4, HALO_BYTES, hbar);
     }
+    if (m.do_surface) ++hcount;
     Spinor<float> src[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
-      if (a.s_in32.p) a.s_in32.load(g, domr, tid + j * NT, src[j]);
+      if (m.first && a.s_in32.p) a.s_in32.load(g, domr, tid + j * NT, src[j]);
       else a.s_in.load(g, domr, tid + j * NT, src[j]);
     }
     if (i == 0) __syncthreads();  // barrier initialisation visible to every thread
     {
-      const bool ok_l = i > 0 || mbar_wait_bounded(lbar, 0);
-      const bool ok_h = !a.do_surface || mbar_wait_bounded(hbar, i & 1);
+      const bool ok_l = i > 0 || mbar_wait_bounded(lbar, spar);
+      const bool ok_h = !m.do_surface || mbar_wait_bounded(hbar, hpar);
       if (__syncthreads_or(!(ok_l && ok_h))) {
-        st_give_up(a.status, tid, !ok_l, lbar, 0, !ok_h, hbar, i & 1);
-        if (i == 0) mbar_wait_bounded(cbar, 0);
-        return;
+        st_give_up(a.status, tid, !ok_l, lbar, spar, !ok_h, hbar, hpar);
+        if (i == 0) mbar_wait_bounded(cbar, spar);
+        return false;
       }
     }
     Spinor<float> acc[SPT];
-    if (a.do_surface) {
+    if (m.do_surface) {
 #pragma unroll
       for (int j = 0; j < SPT; ++j) st_face_tasks<HALF>(g, sl, dom, tid + j * NT, sx);
       __syncthreads();
@@ -563,13 +604,13 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
     }
     if (i == 0) {
       // C_inv is first needed here
-      const bool ok_c = mbar_wait_bounded(cbar, 0);
+      const bool ok_c = mbar_wait_bounded(cbar, spar);
       if (__syncthreads_or(!ok_c)) {
-        st_give_up(a.status, tid, true, cbar, 0, false, cbar, 0);
-        return;
+        st_give_up(a.status, tid, true, cbar, spar, false, cbar, spar);
+        return false;
       }
     }
-    if (a.do_surface) {
+    if (m.do_surface) {
 #pragma unroll
       for (int j = 0; j < SPT; ++j) {
         st_clover<HALF>(sc, tid + j * NT, acc[j]);
@@ -590,7 +631,7 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
     Spinor<float> xk[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; ++j) xk[j] = src[j];
-    const int napp = a.n_jac + (a.do_update ? 1 : 0);
+    const int napp = a.n_jac + (m.do_update ? 1 : 0);
     for (int it = 0; it < napp; ++it) {
       // the x hops start the sum (no zeroing); the t hops' warp-uniform
       // branches follow, then one straight-line stretch (y, z hops and the
@@ -637,21 +678,180 @@ __device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, 
         }
       }
     }
-    if (a.do_halo) {  // sx holds the final iterate
+    if (m.do_halo) {  // sx holds the final iterate
 #pragma unroll
       for (int j = 0; j < SPT; ++j) st_halo_out<HALF>(g, sx, sl, a.halo, dom, rhs_off, tid + j * NT);
     }
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
-      if (a.x_store) a.x.store(g, domr, tid + j * NT, xk[j]);
-      if (a.x_out32.p) a.x_out32.store(g, domr, tid + j * NT, xk[j]);
+      if (m.last && a.x_store) a.x.store(g, domr, tid + j * NT, xk[j]);
+      if (m.last && a.x_out32.p) a.x_out32.store(g, domr, tid + j * NT, xk[j]);
     }
   }
+  return true;
+}
+
+// one launch = one half-sweep: the launch's mode and the CTA's domain
+template <bool HALF, typename SIO, int SPT>
+__device__ __forceinline__ void sap_staged_body(const StagedArgs<HALF, SIO>& a, int blk) {
+  if (loop_idle(a.g) || (a.skip && *(volatile const int*)a.skip)) return;
+  // programmatic dependent launch: the next launch in the stream may start
+  // its CTAs while this grid drains
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  int hcount = 0;
+  sap_staged_item<HALF, SIO, SPT>(a, launch_mode(a), blk, 0, hcount, true, true, false);
 }
 
 template <bool HALF, typename SIO, int SPT>
 __global__ void __launch_bounds__(ST_THREADS / SPT, HALF ? 2 : 1) sap_staged_kernel(StagedArgs<HALF, SIO> a) {
   sap_staged_body<HALF, SIO, SPT>(a, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// M_SAP in one launch: half-sweeps ordered by per-domain flags
+// ---------------------------------------------------------------------------
+// A grid of resident CTAs takes the work items of a whole M_SAP in order
+// from a ticket counter: item j is half-sweep k = j / nhalf (sweep k / 2,
+// colour k % 2) of the colour's domain j % nhalf.  Item (k, d) reads the
+// halo that its eight neighbours (the other colour) wrote in half-sweep
+// k - 1, and the s that its own domain wrote in half-sweep k - 2, which
+// those neighbours' half-sweep k - 1 waited for.  So it waits for the eight
+// neighbours' flags to reach k, and a finished item sets its domain's flag
+// to k + 1 (release after its global writes; the waits acquire).  Its halo
+// writes go to the neighbours' blocks, whose previous readers (their
+// half-sweep k - 1) are among the items it waited for.  Every item depends
+// only on items with smaller tickets, which CTAs that are running hold, so
+// the order cannot deadlock.  Compared with one launch per half-sweep, no
+// CTA waits for a whole grid to drain, and the CTAs' staging copies spread
+// over time instead of coming in bursts at the start of every wave.
+// The last CTA to leave clears the flags and the counters for the next use.
+struct FlowArgs {
+  int* flags;      // [domain]: half-sweeps finished + 1 of its last item (0 at rest)
+  int* ctr;        // [0] ticket, [1] CTAs retired
+  int n_sap;
+  int stagger_ns;  // the second half of the CTAs start this much later
+};
+
+// Bounded acquire-wait for *flag >= need.  Gives up after 2^22 polls or
+// half a second, or as soon as another CTA has reported a failure.
+__device__ __forceinline__ bool flow_wait(const int* flag, int need, const int* status) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < (1 << 22); ++i) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+    if (v >= need) return true;
+    if ((i & 31) == 31) {
+      if (*(volatile const int*)status != 0) return false;
+      if (global_ns() - t0 > 500000000ull) return false;
+    }
+    __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Each CTA holds the ticket after the one it runs, so that, while an item
+// computes, the next item's links and C_inv are already on their way to L2.
+// A finished item's flag is released only after the next item's staging
+// copies are issued (the release waits for the item's writes), and always
+// before the CTA waits on any flag, so no CTA waits while holding an
+// unreleased flag.  Holding the next ticket cannot block anyone for ever:
+// the item in hand depends only on smaller tickets.
+template <bool HALF, typename SIO>
+__global__ void __launch_bounds__(ST_THREADS, HALF ? 2 : 1) sap_flow_kernel(StagedArgs<HALF, SIO> a, FlowArgs f) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using ST = StageT<HALF>;
+  unsigned char* sl = smem + SX_BYTES;
+  unsigned char* sc = sl + ST::LINK_BYTES;
+  uint64_t* lbar = reinterpret_cast<uint64_t*>(sc + ST::CLOV_BYTES);
+  __shared__ int s_item, s_next, s_last;
+  const Geom& g = a.g;
+  if (loop_idle(g) || (a.skip && *(volatile const int*)a.skip)) return;  // the same for every CTA
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // The counters and flags belong to the previous use until its grid has
+  // completed, and the earlier launches' outputs are read below: wait for
+  // the previous grid (which itself waited for its own predecessor) first.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int tid = threadIdx.x;
+  const int nhalf = g.nhalf;
+  const int total = 2 * (f.n_sap + 1) * nhalf;
+  if (f.stagger_ns > 0 && blockIdx.x >= gridDim.x / 2 && tid == 0) {
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < 4096 && global_ns() - t0 < (unsigned long long)f.stagger_ns; ++i) __nanosleep(256);
+  }
+  if (tid == 0) {
+    s_item = atomicAdd(f.ctr, 1);
+    s_next = atomicAdd(f.ctr, 1);
+  }
+  __syncthreads();
+  int j = s_item, jn = s_next;
+  int use = 0, hcount = 0;
+  int pending = -1, pending_val = 0;  // (thread 0) finished item whose flag is not yet released
+  auto release = [&]() {
+    if (pending >= 0) {
+      __threadfence();
+      asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f.flags + pending), "r"(pending_val) : "memory");
+      pending = -1;
+    }
+  };
+  while (j < total) {
+    const int k = j / nhalf, blk = j - k * nhalf;
+    const int sweep = k >> 1, colour = k & 1;
+    const ItemMode m{colour, k > 0, sweep < f.n_sap, sweep == 0, sweep == f.n_sap,
+                     !(sweep == f.n_sap && colour == 1)};
+    const int dom = colour * nhalf + blk;
+    if (tid == 0) {
+      // the staging copies need nothing from other items: issue them first
+      st_issue_staging(a, dom, use, sl, sc, lbar, lbar + 1, lbar + 2);
+      if (jn < total) {
+        const int kn = jn / nhalf;
+        const int domn = (kn & 1) * nhalf + (jn - kn * nhalf);
+        prefetch_l2(a.links + (size_t)domn * ST::LINK_BYTES, ST::LINK_BYTES);
+        prefetch_l2(a.clov + (size_t)domn * ST::CLOV_BYTES, ST::CLOV_BYTES);
+      }
+      release();
+    }
+    if (k > 0) {
+      // warp 1 waits for the neighbours while warp 0 releases
+      bool ok = true;
+      if (tid >= 32 && tid < 40) ok = flow_wait(f.flags + __ldg(g.nbr + dom * 8 + (tid - 32)), k, a.status);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.status, QCD_ERR_TIMEOUT);
+        mbar_wait_bounded(lbar, use & 1);
+        mbar_wait_bounded(lbar + 1, use & 1);
+        break;
+      }
+    }
+    if (!sap_staged_item<HALF, SIO, 1>(a, m, blk, use, hcount, false, false, true)) break;
+    __syncthreads();  // the item's global writes are done and its shared memory is free
+    if (tid == 0) {
+      pending = dom;
+      pending_val = k + 1;
+      s_item = jn;
+      s_next = (jn >= total || *(volatile const int*)a.status != 0) ? total : atomicAdd(f.ctr, 1);
+    }
+    __syncthreads();
+    j = s_item;
+    jn = s_next;
+    ++use;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    release();
+    __threadfence();
+    s_last = atomicAdd(f.ctr + 1, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int d = tid; d < g.ndom; d += blockDim.x) f.flags[d] = 0;
+    if (tid == 0) {
+      f.ctr[0] = 0;
+      f.ctr[1] = 0;
+    }
+  }
 }
 
 // Ragged batch: one launch covers one half-sweep of every lattice.  Block b
@@ -744,6 +944,14 @@ void build_sap_staging(qcd_ctx* ctx, cudaStream_t st) {
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
     QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_staged_kernel<false, F32Spinor, 2>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_flow_kernel<true, F16Spinor>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_flow_kernel<true, F32Spinor>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s16));
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(sap_flow_kernel<false, F32Spinor>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
+    QCD_CUDA_CHECK(cudaMalloc(&ctx->flow_state, sizeof(int) * (2 + nd)));
+    QCD_CUDA_CHECK(cudaMemset(ctx->flow_state, 0, sizeof(int) * (2 + nd)));
   }
   LaunchScope ls(ctx, QCD_KC_OTHER, st);
   build_link_stage_kernel<<<grid_for(g.vol * 4, 256), 256, 0, st>>>(g, ctx->u64, (__half2*)ctx->st_link16,
@@ -805,6 +1013,54 @@ static void staged_sequence_shape(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, S
   }
 }
 
+// Algorithm 1 as one launch of resident CTAs (sap_flow_kernel).
+template <bool HALF, typename SIO>
+static void flow_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b, F32Spinor x_out32,
+                          float4* halo, int nrhs, int n_sap, int n_jac, cudaStream_t st, int stagger_ns) {
+  QCD_REQUIRE(n_sap >= 1 && 2 * (n_sap + 1) * (long long)ctx->geom.nhalf < (1LL << 31) && n_sap < (1 << 20),
+              QCD_ERR_ARG, "one-launch SAP: n_sap out of range");
+  StagedArgs<HALF, SIO> a;
+  a.g = ctx->geom;
+  a.colour = 0;
+  a.n_jac = n_jac;
+  a.do_surface = a.do_update = a.do_halo = 0;  // per item
+  a.nrhs = nrhs;
+  a.kappa = (float)ctx->kappa;
+  a.s_in = s;
+  a.s_out = s;
+  a.x = x;
+  a.b = b;
+  a.s_in32 = s_first_in32;
+  a.x_out32 = x_out32;
+  a.x_store = x_out32.p ? 0 : 1;
+  a.halo = halo;
+  a.links = (const unsigned char*)(HALF ? ctx->st_link16 : ctx->st_link32);
+  a.clov = (const unsigned char*)(HALF ? ctx->st_clov16 : ctx->st_clov32);
+  a.status = ctx->d_status;
+  a.extra_tx = ctx->inject == QCD_INJECT_STAGING_WAIT ? 16 : 0;
+  a.extra_htx = ctx->inject == QCD_INJECT_HALO_WAIT ? 16 : 0;
+  a.skip = nullptr;
+  FlowArgs f;
+  f.flags = ctx->flow_state + 2;
+  f.ctr = ctx->flow_state;
+  f.n_sap = n_sap;
+  f.stagger_ns = stagger_ns;
+  // every CTA of the grid must be resident at once: as many as fit
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    QCD_CUDA_CHECK(cudaGetDevice(&dev));
+    QCD_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QCD_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sap_flow_kernel<HALF, SIO>, ST_THREADS,
+                                                                 st_smem_bytes<HALF>()));
+  }
+  const int total = 2 * (n_sap + 1) * ctx->geom.nhalf;
+  const int grid = std::max(1, std::min(total, per_sm * sms));
+  LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
+  launch_pdl(sap_flow_kernel<HALF, SIO>, dim3(grid), dim3(ST_THREADS), st_smem_bytes<HALF>(), st, a, f);
+  check_launch();
+}
+
 // The block-kernel shape is chosen by the autotuner on the first M_SAP of
 // each precision, lattice, right-hand-side count and n_jac: it times the
 // whole sequence in every shape on the caller's buffers (M_SAP is a function
@@ -814,7 +1070,12 @@ static void staged_sequence_shape(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, S
 // domain's links and C_inv for itself; more CTAs where a lattice has too few
 // domains to fill the GPU) instead of one CTA running all of them through
 // its staged operator.  qcd_set_sap_shape fixes the shape.
-static const char* const kSapShapes[] = {"256x1site", "128x2sites", "256x1site_rhs_grid"};
+// The last two shapes run the whole of M_SAP in one launch (sap_flow_kernel),
+// the second of them with half of its CTAs starting later, so that the
+// CTAs on one SM load their operators at different times.
+static const char* const kSapShapes[] = {"256x1site", "128x2sites", "256x1site_rhs_grid", "one_launch",
+                                         "one_launch_staggered"};
+constexpr int kFlowStaggerNs = 10000;
 
 template <bool HALF, typename SIO>
 static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F32Spinor b, F32Spinor x_out32,
@@ -822,6 +1083,9 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
   auto run = [&](int v) {
     if (v == 1)
       staged_sequence_shape<HALF, SIO, 2>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st);
+    else if (v >= 3 && n_sap >= 1)
+      flow_sequence<HALF, SIO>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st,
+                               v == 4 ? kFlowStaggerNs : 0);
     else
       staged_sequence_shape<HALF, SIO, 1>(ctx, s_first_in32, s, x, b, x_out32, halo, nrhs, n_sap, n_jac, st,
                                           v == 2 && nrhs > 1);
@@ -833,7 +1097,14 @@ static void staged_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, 
     std::snprintf(key, sizeof key, "sap_staged_%s L%dx%dx%dx%d nrhs%d n_sap%d n_jac%d",
                   HALF ? (std::is_same<SIO, F16Spinor>::value ? "f16" : "f16gauge") : "f32", g.L[0], g.L[1], g.L[2],
                   g.L[3], nrhs, n_sap, n_jac);
-    v = tune_pick(ctx, key, nrhs > 1 ? 3 : 2, kSapShapes, run, st);
+    // candidates: both thread shapes, the right-hand-side grid (several
+    // right-hand sides only) and, with n_sap >= 1, the two one-launch forms
+    static const int with_rhs[] = {0, 1, 2, 3, 4}, one_rhs[] = {0, 1, 3, 4};
+    const int* cand = nrhs > 1 ? with_rhs : one_rhs;
+    const int nc = (nrhs > 1 ? 3 : 2) + (n_sap >= 1 ? 2 : 0);
+    const char* names[5];
+    for (int c = 0; c < nc; ++c) names[c] = kSapShapes[cand[c]];
+    v = cand[tune_pick(ctx, key, nc, names, [&](int c) { run(cand[c]); }, st)];
   }
   run(v);
 }

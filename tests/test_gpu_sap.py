@@ -112,7 +112,7 @@ def test_sap_kernel_shapes_agree_bit_for_bit(wide, sap_prec):
     srcs = np.stack([wide.source(2121 + r) for r in range(2)])
     out = {}
     try:
-        for shape in (0, 1, 2):
+        for shape in (0, 1, 2, 3, 4):
             B.qcd_set_sap_shape(ctx, shape)
             out[shape] = (to_np(wide.lat.sap(b, 4, 4, sap_prec)), to_np(wide.lat.sap(srcs, 4, 4, sap_prec, nrhs=2)))
         B.qcd_set_sap_shape(ctx, -1)
@@ -120,7 +120,7 @@ def test_sap_kernel_shapes_agree_bit_for_bit(wide, sap_prec):
         tuned2 = to_np(wide.lat.sap(srcs, 4, 4, sap_prec, nrhs=2))
     finally:
         B.qcd_set_sap_shape(ctx, -1)
-    for shape in (1, 2):
+    for shape in (1, 2, 3, 4):
         assert np.array_equal(out[0][0], out[shape][0])
         assert np.array_equal(out[0][1], out[shape][1])
     assert np.array_equal(tuned2, out[0][1])
@@ -129,13 +129,86 @@ def test_sap_kernel_shapes_agree_bit_for_bit(wide, sap_prec):
     assert rel_l2(out[1][0], sap.msap(wide.op, b, 4, 4)) <= tol
     rep = B.qcd_tuning_report(ctx)
     line = [ln for ln in rep.splitlines() if ln.startswith("sap_staged_")]
-    assert line and "256x1site" in line[0] and "128x2sites" in line[0]
-    assert any("nrhs2" in ln and "256x1site_rhs_grid" in ln for ln in line)
+    assert line and "256x1site" in line[0] and "128x2sites" in line[0] and "one_launch" in line[0]
+    assert any("nrhs2" in ln and "256x1site_rhs_grid" in ln and "one_launch_staggered" in ln for ln in line)
+
+
+@pytest.fixture(scope="module")
+def cube8():
+    """8^4 with 4^4 domains: eight domains per colour, so a one-launch M_SAP
+    runs many more CTAs than a half-sweep has domains, and most items wait
+    on their neighbours' flags."""
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), eps=0.3, kappa=0.12, csw=1.0, seed=1131)
+    yield p
+    p.close()
+
+
+@pytest.mark.parametrize("lattice", ["wide", "cube8"])
+@pytest.mark.parametrize("sap_prec", ["single", "half_gauge", "half"])
+@pytest.mark.parametrize("n_sap,n_jac", [(1, 1), (2, 4), (4, 4)])
+def test_sap_one_launch_matches_per_launch(request, lattice, sap_prec, n_sap, n_jac):
+    """M_SAP in one launch (shapes 3 and 4: resident CTAs taking (half-sweep,
+    domain) items in order, each waiting for its eight neighbours' flags)
+    does every domain's half-sweeps with the per-launch kernel's arithmetic
+    in the same order of dependencies, so M_SAP and A M_SAP agree bit for bit
+    with shape 0, for one and for three right-hand sides, and stay so on a
+    second call (the counters and flags are cleared by the last CTA)."""
+    from paper_2109_10687_gb300 import binding as B
+    p = request.getfixturevalue(lattice)
+    ctx = p.lat.ctx
+    b = p.source(2140)
+    srcs = np.stack([p.source(2141 + r) for r in range(3)])
+    out = {}
+    try:
+        for shape in (0, 3, 4, 3):
+            B.qcd_set_sap_shape(ctx, shape)
+            out.setdefault(shape, []).append((to_np(p.lat.sap(b, n_sap, n_jac, sap_prec)),
+                                              to_np(p.lat.sap(b, n_sap, n_jac, sap_prec, with_A=True)),
+                                              to_np(p.lat.sap(srcs, n_sap, n_jac, sap_prec, nrhs=3))))
+            assert B.qcd_device_status(ctx) == B.QCD_OK
+    finally:
+        B.qcd_set_sap_shape(ctx, -1)
+    ref = out[0][0]
+    for shape in (3, 4):
+        for got in out[shape]:
+            for g_, r_ in zip(got, ref):
+                assert np.array_equal(g_, r_), (shape, lattice)
+    tol = 1e-5 if sap_prec == "single" else 5e-3
+    assert rel_l2(out[3][0][0], sap.msap(p.op, b, n_sap, n_jac)) <= tol
+
+
+@pytest.mark.parametrize("hook,prec", [("staging", "half"), ("halo", "half_gauge")])
+def test_one_launch_wait_timeout_is_reported_and_context_survives(cube8, hook, prec):
+    """The one-launch M_SAP's failure path, without a GPU fault: a test hook
+    makes the staging (or halo) wait expect 16 bytes that no copy brings.
+    Every item that meets it gives up after half a second and records
+    QCD_ERR_TIMEOUT; the other CTAs see the status, stop waiting for flags
+    and leave; the last one clears the counters and flags.  With the hook
+    cleared, the same context's next one-launch M_SAP is correct."""
+    from paper_2109_10687_gb300 import binding as B
+    ctx = cube8.lat.ctx
+    b = cube8.source(2150)
+    inj = B.INJECT_STAGING_WAIT if hook == "staging" else B.INJECT_HALO_WAIT
+    try:
+        B.qcd_set_sap_shape(ctx, 3)
+        B.qcd_test_inject(ctx, inj)
+        cube8.lat.sap(b, 1, 1, prec)
+        assert B.qcd_device_status(ctx, reset=True) == B.QCD_ERR_TIMEOUT
+        B.qcd_test_inject(ctx, B.INJECT_NONE)
+        got = to_np(cube8.lat.sap(b, 4, 4, prec))
+        assert B.qcd_device_status(ctx) == B.QCD_OK
+        B.qcd_set_sap_shape(ctx, 0)
+        ref = to_np(cube8.lat.sap(b, 4, 4, prec))
+        assert np.array_equal(got, ref)
+    finally:
+        B.qcd_test_inject(ctx, B.INJECT_NONE)
+        B.qcd_device_status(ctx, reset=True)
+        B.qcd_set_sap_shape(ctx, -1)
 
 
 def test_sap_shape_rejects_unknown_value(wide):
     from paper_2109_10687_gb300 import binding as B
-    assert B.lib().qcd_set_sap_shape(wide.lat.ctx, 3) == B.QCD_ERR_ARG
+    assert B.lib().qcd_set_sap_shape(wide.lat.ctx, 5) == B.QCD_ERR_ARG
     assert B.lib().qcd_set_sap_shape(wide.lat.ctx, -2) == B.QCD_ERR_ARG
 
 

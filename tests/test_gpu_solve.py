@@ -88,16 +88,19 @@ def test_double_float_residual_bound(kappa, seed):
         p.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, -1])
-def test_solve_with_each_sap_kernel_shape(c1, c1_ref, shape):
+@pytest.mark.parametrize("use_graph", [0, 2])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, -1])
+def test_solve_with_each_sap_kernel_shape(c1, c1_ref, shape, use_graph):
     """The solve with each shape of the SAP block kernel (one or two sites
-    per thread, or the autotuned one) reaches the float64 true residual 1e-10
-    recomputed by the oracle, with the same iterations."""
+    per thread, one CTA per right-hand side, M_SAP in one launch with or
+    without staggered CTAs, or the autotuned one), with a host loop and with
+    the device-side graph loop, reaches the float64 true residual 1e-10
+    recomputed by the oracle."""
     from paper_2109_10687_gb300 import binding as B
     b, x_ref = c1_ref
     try:
         B.qcd_set_sap_shape(c1.lat.ctx, shape)
-        x, rc, info = c1.lat.solve(b, tol=1e-10, sap_prec="half", inner_tol=1e-5)
+        x, rc, info = c1.lat.solve(b, tol=1e-10, sap_prec="half", inner_tol=1e-5, use_graph=use_graph)
     finally:
         B.qcd_set_sap_shape(c1.lat.ctx, -1)
     assert rc == 0
