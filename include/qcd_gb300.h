@@ -95,16 +95,22 @@ typedef struct qcd_solve_params {
                           while node (no host round trip per iteration)      */
   int x_is_guess;      /* 1: x holds an initial guess on entry (resume)      */
   int residual_prec;   /* precision of x, r = b - D x and D in Algorithm 4:
-                          1 native float64 (default), 0 double-float (two
-                          float32, ~48 bits, on the float32 pipes)           */
+                          0 double-float (default: two float32, ~48 bits,
+                          on the float32 pipes, which on this GPU are far
+                          wider than the float64 ones; the residual it
+                          stops on is within 2^-48 (1 + 300 |x| / |b|) of
+                          the float64 residual of the same x), 1 native
+                          float64; other values QCD_ERR_ARG.  The flexible
+                          GMRES outer iteration and the shared-launch batch
+                          solve compute in native float64 either way.       */
   int outer_restart;   /* outer iteration: 0 (default) the defect correction
                           of Algorithm 4; m >= 1 flexible GMRES with restart
                           length m, in float64, each inner SAP-BiCGStab
                           solve acting as a preconditioner that may change
                           from step to step (the flexible outer solver Sec. 3
                           names as an alternative to Algorithm 4; max_outer
-                          then counts its steps).  Requires nrhs = 1 and
-                          residual_prec = 1, else QCD_ERR_ARG.               */
+                          then counts its steps).  Requires nrhs = 1, else
+                          QCD_ERR_ARG.                                       */
 } qcd_solve_params;
 
 /* Results of qcd_solve, one entry per right-hand side where indicated. */
@@ -277,7 +283,7 @@ int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int on_device,
 
 /* Fill params with defaults: tol 1e-10, inner_tol 1e-6, max_outer 20,
  * max_inner 500, n_sap 4, n_jac 4, sap_prec SINGLE, use_graph 0,
- * x_is_guess 0, residual_prec 1 (float64), outer_restart 0 (Algorithm 4). */
+ * x_is_guess 0, residual_prec 0 (double-float), outer_restart 0 (Algorithm 4). */
 int qcd_solve_params_default(qcd_solve_params* params);
 
 /* ---- ragged batches of lattices --------------------------------------- */
@@ -300,8 +306,9 @@ int qcd_batch_apply_D(qcd_batch* batch, void* const* out, const void* const* in,
 /* Solve D_i x_i = b_i for every lattice (one right-hand side each, canonical
  * float64 fields as in qcd_solve; Algorithm 4 around Algorithm 5 on
  * A M_SAP, Sec. 3).  When every lattice has 4^4 domains (and no SAP domains
- * of its own, see qcd_set_sap_domain), outer_restart = 0 and
- * residual_prec = 1, the lattices are solved in SHARED LAUNCHES: each
+ * of its own, see qcd_set_sap_domain) and outer_restart = 0, the lattices
+ * are solved in SHARED LAUNCHES (with the residual in native float64 for
+ * either residual_prec): each
  * SAP half-sweep (Algorithm 1), each application of A and of the float64 D,
  * and each fused BLAS-1 step of Algorithm 5 is one kernel launch over every
  * lattice, through work lists built on the first call; the inner loop is one

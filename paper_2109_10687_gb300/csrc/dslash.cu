@@ -456,73 +456,71 @@ void ablock_launch(qcd_ctx* ctx, float4* out, const float4* in, int row, int col
 // consecutive sites share one colour; 64 sites per block.
 constexpr int DF_SITES = 64;
 
-// neighbour (domain, site, sign) of hop (MU, FWD), selected without branches
-template <int MU, bool FWD>
-__device__ __forceinline__ void df_nbr(const Geom& g, int dom, int s, const int nb[8], int tf, int& nd, int& ns,
-                                       bool& neg) {
-  const int c = (s >> g.shift[MU]) & (g.d[MU] - 1);
-  const int step = 1 << g.shift[MU];
-  const int span = (g.d[MU] - 1) * step;
-  const bool inside = FWD ? c < g.d[MU] - 1 : c > 0;
-  nd = inside ? dom : nb[2 * MU + (FWD ? 0 : 1)];
-  ns = inside ? (FWD ? s + step : s - step) : (FWD ? s - span : s + span);
-  neg = !inside && ((tf >> (2 * MU + (FWD ? 0 : 1))) & 1) && g.bc_t < 0;
+// Code size matters more than anything else here: written out for all
+// eight hops and three colour rows, a thread's double-float arithmetic is
+// several thousand instructions that the instruction cache cannot hold, and
+// the warps wait on instruction fetch.  So the hops run in a loop: the
+// neighbour lookup, the loads and the complex multiply-adds are one piece
+// of code for every hop, and only the spin projection and reconstruction,
+// which differ by direction, go through a switch to their fixed forms; the
+// clover rows read their entries by a row index known at run time.  The
+// arithmetic and its order are those of the fully written-out form.
+
+// neighbour (domain, site, sign) of hop (mu, fwd), selected without branches
+__device__ __forceinline__ void df_nbr(const Geom& g, int mu, bool fwd, int dom, int s, const int nb[8], int tf,
+                                       int& nd, int& ns, bool& neg) {
+  const int c = (s >> g.shift[mu]) & (g.d[mu] - 1);
+  const int step = 1 << g.shift[mu];
+  const int span = (g.d[mu] - 1) * step;
+  const bool inside = fwd ? c < g.d[mu] - 1 : c > 0;
+  const int k = 2 * mu + (fwd ? 0 : 1);
+  nd = inside ? dom : nb[k];
+  ns = inside ? (fwd ? s + step : s - step) : (fwd ? s - span : s + span);
+  neg = !inside && ((tf >> k) & 1) && g.bc_t < 0;
 }
 
 __device__ __forceinline__ float4 df_pack(cx<df64> v) { return make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
 __device__ __forceinline__ cx<df64> df_unpack(float4 v) { return make_cx(df64(v.x, v.y), df64(v.z, v.w)); }
 
-// phase 1: rows (h0, h1) of colour a of the projected neighbour, signed
+// the projection of hop (MU, FWD): its fixed spin pattern
 template <int MU, bool FWD>
-__device__ __forceinline__ void df_project(const Geom& g, const DF64Spinor& in, int dom, int s, int a,
+__device__ __forceinline__ void df_proj(const cx<df64> q[4], cx<df64>& h0, cx<df64>& h1) {
+  project1<MU, FWD ? -1 : +1>(q[0], q[1], q[2], q[3], h0, h1);
+}
+
+// phase 1: rows (h0, h1) of colour a of the projected neighbour, signed
+__device__ __forceinline__ void df_project(const Geom& g, const DF64Spinor& in, int hop, int dom, int s, int a,
                                            const int nb[8], int tf, float4* sh, int sl) {
   int nd, ns;
   bool neg;
-  df_nbr<MU, FWD>(g, dom, s, nb, tf, nd, ns, neg);
+  df_nbr(g, hop >> 1, !(hop & 1), dom, s, nb, tf, nd, ns, neg);
   cx<df64> q[4];
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) q[sp] = df_unpack(__ldg(in.p + in.idx(g, nd, sp * 3 + a, ns)));
   cx<df64> h0, h1;
-  project1<MU, FWD ? -1 : +1>(q[0], q[1], q[2], q[3], h0, h1);
+  switch (hop) {
+    case 0: df_proj<0, true>(q, h0, h1); break;
+    case 1: df_proj<0, false>(q, h0, h1); break;
+    case 2: df_proj<1, true>(q, h0, h1); break;
+    case 3: df_proj<1, false>(q, h0, h1); break;
+    case 4: df_proj<2, true>(q, h0, h1); break;
+    case 5: df_proj<2, false>(q, h0, h1); break;
+    case 6: df_proj<3, true>(q, h0, h1); break;
+    default: df_proj<3, false>(q, h0, h1); break;
+  }
   if (neg) {  // exact: a sign flip of both parts
     h0 = make_cx(-h0.re, -h0.im);
     h1 = make_cx(-h1.re, -h1.im);
   }
-  constexpr int hop = 2 * MU + (FWD ? 0 : 1);
   sh[((hop * 2 + 0) * 3 + a) * DF_SITES + sl] = df_pack(h0);
   sh[((hop * 2 + 1) * 3 + a) * DF_SITES + sl] = df_pack(h1);
 }
 
-// phase 2: row a of U h (forward) or U^dag h (backward), rebuilt into colour a
+// the reconstruction of hop (MU, FWD) into the four spins of one colour
+// (the rules of accumulate())
 template <int MU, bool FWD>
-__device__ __forceinline__ void df_mul_acc(const Geom& g, const LinkPtr<df64>& U, int dom, int s, int a,
-                                           const int nb[8], int tf, const float4* sh, int sl, cx<df64> acc[4]) {
-  int nd, ns;
-  bool neg;
-  df_nbr<MU, FWD>(g, dom, s, nb, tf, nd, ns, neg);
-  constexpr int hop = 2 * MU + (FWD ? 0 : 1);
-  cx<df64> row[3];
-  {
-    const size_t base = ((size_t)(((FWD ? dom : nd) * 4 + MU) * 9)) << g.logvd;
-    const int site = FWD ? s : ns;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int e = FWD ? a * 3 + b : b * 3 + a;
-      const float4 v = __ldg(U.p + base + ((size_t)e << g.logvd) + site);
-      row[b] = FWD ? make_cx(df64(v.x, v.y), df64(v.z, v.w)) : make_cx(df64(v.x, v.y), -df64(v.z, v.w));
-    }
-  }
-  cx<df64> uh[2];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    cx<df64> t = row[0] * df_unpack(sh[((hop * 2 + r) * 3 + 0) * DF_SITES + sl]);
-    t = cmac(t, row[1], df_unpack(sh[((hop * 2 + r) * 3 + 1) * DF_SITES + sl]));
-    t = cmac(t, row[2], df_unpack(sh[((hop * 2 + r) * 3 + 2) * DF_SITES + sl]));
-    uh[r] = t;
-  }
-  // rebuild the four spins of colour a (the rules of accumulate())
+__device__ __forceinline__ void df_rebuild(cx<df64> h0, cx<df64> h1, cx<df64> acc[4]) {
   constexpr int PM = FWD ? -1 : +1;
-  const cx<df64> h0 = uh[0], h1 = uh[1];
   acc[0] = acc[0] + h0;
   acc[1] = acc[1] + h1;
   if (MU == 0) {
@@ -540,29 +538,66 @@ __device__ __forceinline__ void df_mul_acc(const Geom& g, const LinkPtr<df64>& U
   }
 }
 
-template <int A>
-__device__ __forceinline__ void df_clover_rows(const Geom& g, const DF64Spinor& in, const CloverPtrDF64& clov, int dom,
-                                               int s, cx<df64> res[4]) {
+// phase 2: row a of U h (forward) or U^dag h (backward), rebuilt into colour a
+__device__ __forceinline__ void df_mul_acc(const Geom& g, const LinkPtr<df64>& U, int hop, int dom, int s, int a,
+                                           const int nb[8], int tf, const float4* sh, int sl, cx<df64> acc[4]) {
+  const int mu = hop >> 1;
+  const bool fwd = !(hop & 1);
+  int nd, ns;
+  bool neg;
+  df_nbr(g, mu, fwd, dom, s, nb, tf, nd, ns, neg);
+  cx<df64> row[3];
+  {
+    const size_t base = ((size_t)(((fwd ? dom : nd) * 4 + mu) * 9)) << g.logvd;
+    const int site = fwd ? s : ns;
 #pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    cx<df64> xv[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) xv[j] = df_unpack(__ldg(in.p + in.idx(g, dom, (2 * b + j / 3) * 3 + j % 3, s)));
-    CloverBlockDF64 blk;
-    clov.load_block(g, dom, s, b, blk);
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int i = 3 * r + A;
-      cx<df64> y = make_cx(df64(0.f), df64(0.f));
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (j == i) y = make_cx(fma(blk.diagv(i), xv[j].re, y.re), fma(blk.diagv(i), xv[j].im, y.im));
-        else if (j > i) y = cmac(y, blk.off(herm_off(i, j)), xv[j]);
-        else y = cmacc(y, blk.off(herm_off(j, i)), xv[j]);
-      }
-      res[2 * b + r] = y;
+    for (int b = 0; b < 3; ++b) {
+      const int e = fwd ? a * 3 + b : b * 3 + a;
+      const float4 v = __ldg(U.p + base + ((size_t)e << g.logvd) + site);
+      row[b] = fwd ? make_cx(df64(v.x, v.y), df64(v.z, v.w)) : make_cx(df64(v.x, v.y), -df64(v.z, v.w));
     }
   }
+  cx<df64> uh[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    cx<df64> t = row[0] * df_unpack(sh[((hop * 2 + r) * 3 + 0) * DF_SITES + sl]);
+    t = cmac(t, row[1], df_unpack(sh[((hop * 2 + r) * 3 + 1) * DF_SITES + sl]));
+    t = cmac(t, row[2], df_unpack(sh[((hop * 2 + r) * 3 + 2) * DF_SITES + sl]));
+    uh[r] = t;
+  }
+  switch (hop) {
+    case 0: df_rebuild<0, true>(uh[0], uh[1], acc); break;
+    case 1: df_rebuild<0, false>(uh[0], uh[1], acc); break;
+    case 2: df_rebuild<1, true>(uh[0], uh[1], acc); break;
+    case 3: df_rebuild<1, false>(uh[0], uh[1], acc); break;
+    case 4: df_rebuild<2, true>(uh[0], uh[1], acc); break;
+    case 5: df_rebuild<2, false>(uh[0], uh[1], acc); break;
+    case 6: df_rebuild<3, true>(uh[0], uh[1], acc); break;
+    default: df_rebuild<3, false>(uh[0], uh[1], acc); break;
+  }
+}
+
+// (1 + C) x, row i of block b (i = 3 r + a, known at run time): the block's
+// packed reals come straight from memory, the diagonal one as a real
+// factor and the off-diagonal ones conjugated below the diagonal
+__device__ __forceinline__ cx<df64> df_clover_row(const Geom& g, const DF64Spinor& in, const CloverPtrDF64& clov,
+                                                  int dom, int s, int b, int i) {
+  const float4* cp = clov.p + (((size_t)(dom * 36 + 18 * b)) << g.logvd) + s;
+  cx<df64> y = make_cx(df64(0.f), df64(0.f));
+#pragma unroll 1
+  for (int j = 0; j < 6; ++j) {
+    const cx<df64> xj = df_unpack(__ldg(in.p + in.idx(g, dom, (2 * b + j / 3) * 3 + j % 3, s)));
+    if (j == i) {
+      const float4 v = __ldg(cp + ((size_t)(i >> 1) << g.logvd));
+      const df64 d = (i & 1) ? df64(v.z, v.w) : df64(v.x, v.y);
+      y = make_cx(fma(d, xj.re, y.re), fma(d, xj.im, y.im));
+    } else {
+      const int k = j > i ? herm_off(i, j) : herm_off(j, i);
+      const cx<df64> c = df_unpack(__ldg(cp + ((size_t)(3 + k) << g.logvd)));
+      y = j > i ? cmac(y, c, xj) : cmacc(y, c, xj);
+    }
+  }
+  return y;
 }
 
 __global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
@@ -589,35 +624,21 @@ __global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spin
     nb[4] = n1.x; nb[5] = n1.y; nb[6] = n1.z; nb[7] = n1.w;
   }
   const int tf = __ldg(g.tflag + dom);
-  df_project<0, true>(g, inr, dom, s, a, nb, tf, sh, sl);
-  df_project<0, false>(g, inr, dom, s, a, nb, tf, sh, sl);
-  df_project<1, true>(g, inr, dom, s, a, nb, tf, sh, sl);
-  df_project<1, false>(g, inr, dom, s, a, nb, tf, sh, sl);
-  df_project<2, true>(g, inr, dom, s, a, nb, tf, sh, sl);
-  df_project<2, false>(g, inr, dom, s, a, nb, tf, sh, sl);
-  df_project<3, true>(g, inr, dom, s, a, nb, tf, sh, sl);
-  df_project<3, false>(g, inr, dom, s, a, nb, tf, sh, sl);
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) df_project(g, inr, hop, dom, s, a, nb, tf, sh, sl);
   __syncthreads();
   cx<df64> acc[4];
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) acc[sp] = make_cx(df64(0.f), df64(0.f));
-  df_mul_acc<0, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
-  df_mul_acc<0, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
-  df_mul_acc<1, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
-  df_mul_acc<1, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
-  df_mul_acc<2, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
-  df_mul_acc<2, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
-  df_mul_acc<3, true>(g, U, dom, s, a, nb, tf, sh, sl, acc);
-  df_mul_acc<3, false>(g, U, dom, s, a, nb, tf, sh, sl, acc);
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) df_mul_acc(g, U, hop, dom, s, a, nb, tf, sh, sl, acc);
   if (!live) return;
-  // (1 + C) x, rows (block b, spin-in-block r, colour a): index i = 3 r + a;
-  // a is warp-uniform, and a compile-time row keeps the block in registers
+  // (1 + C) x, rows (block b, spin-in-block r, colour a): index i = 3 r + a
   cx<df64> res[4];
-  switch (a) {
-    case 0: df_clover_rows<0>(g, inr, clov, dom, s, res); break;
-    case 1: df_clover_rows<1>(g, inr, clov, dom, s, res); break;
-    default: df_clover_rows<2>(g, inr, clov, dom, s, res); break;
-  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) res[2 * b + r] = df_clover_row(g, inr, clov, dom, s, b, 3 * r + a);
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) {
     const cx<df64> o = make_cx(fma(-kappa, acc[sp].re, res[sp].re), fma(-kappa, acc[sp].im, res[sp].im));

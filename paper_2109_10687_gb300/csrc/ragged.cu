@@ -79,7 +79,7 @@ void ragged_free(RaggedWS* w) {
 }
 
 bool ragged_eligible(const std::vector<qcd_ctx*>& ctx, const qcd_solve_params& P) {
-  if (P.outer_restart != 0 || P.residual_prec != 1) return false;
+  if (P.outer_restart != 0) return false;  // the residual is float64 here whatever residual_prec says
   for (const qcd_ctx* c : ctx)
     if (!c->have_gauge || !c->have_clover || !sap_staged_available(c) || c->sap_general) return false;
   return true;

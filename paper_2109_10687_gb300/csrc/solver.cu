@@ -839,7 +839,7 @@ extern "C" int qcd_solve_params_default(qcd_solve_params* p) {
   p->sap_prec = QCD_PREC_SINGLE;
   p->use_graph = 0;
   p->x_is_guess = 0;
-  p->residual_prec = 1;
+  p->residual_prec = 0;
   p->outer_restart = 0;
   return QCD_OK;
 }
@@ -965,8 +965,8 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   QCD_REQUIRE(P.sap_prec == QCD_PREC_SINGLE || P.sap_prec == QCD_PREC_HALF || P.sap_prec == QCD_PREC_HALF_GAUGE,
               QCD_ERR_ARG, "qcd_solve: sap_prec must be SINGLE, HALF or HALF_GAUGE");
   QCD_REQUIRE(P.outer_restart >= 0 && P.outer_restart <= 64, QCD_ERR_ARG, "qcd_solve: outer_restart in [0, 64]");
-  QCD_REQUIRE(P.outer_restart == 0 || (nrhs == 1 && P.residual_prec == 1), QCD_ERR_ARG,
-              "qcd_solve: flexible GMRES needs nrhs = 1 and residual_prec = 1");
+  QCD_REQUIRE(P.residual_prec == 0 || P.residual_prec == 1, QCD_ERR_ARG, "qcd_solve: residual_prec must be 0 or 1");
+  QCD_REQUIRE(P.outer_restart == 0 || nrhs == 1, QCD_ERR_ARG, "qcd_solve: flexible GMRES needs nrhs = 1");
   cudaStream_t st = (cudaStream_t)stream;
   if (P.use_graph) {
     // stream capture is not possible on the legacy default stream: run the
@@ -993,8 +993,9 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     k_norm2_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, n2, d_red, w->partials, w->counters);
     check_launch();
   }
-  // residual precision: native float64 (default) or double-float on the float32 pipes
-  const bool df = P.residual_prec == 0;
+  // residual precision: double-float on the float32 pipes (default) or native
+  // float64; the flexible GMRES outer iteration is float64 throughout
+  const bool df = P.residual_prec == 0 && P.outer_restart == 0;
   float4* bdf = reinterpret_cast<float4*>(w->t64);
   float4* xdf = reinterpret_cast<float4*>(w->x64);
   float4* rdf = reinterpret_cast<float4*>(w->r64);

@@ -51,6 +51,7 @@ def test_solve_defaults_match_header(lib):
     binding._lib = None
     p = binding.qcd_solve_params_default()
     assert (p.tol, p.inner_tol, p.max_outer, p.max_inner, p.n_sap, p.n_jac) == (1e-10, 1e-6, 20, 500, 4, 4)
+    assert (p.sap_prec, p.use_graph, p.x_is_guess, p.residual_prec, p.outer_restart) == (binding.PREC_SINGLE, 0, 0, 0, 0)
 
 
 def test_solve_params_layout_matches_header():

@@ -49,7 +49,14 @@ def test_solve_to_1e10(c1, c1_ref, sap_prec, use_graph):
 
 @pytest.mark.parametrize("residual_prec", [0, 1])
 def test_solve_residual_precisions(c1, c1_ref, residual_prec):
-    """Algorithm 4 with its residual in double-float (0) or native float64 (1)."""
+    """Algorithm 4 with its residual in double-float (0, the default) or
+    native float64 (1); other values are rejected."""
+    from paper_2109_10687_gb300 import binding as B
+    if residual_prec == 0:
+        assert B.qcd_solve_params_default().residual_prec == 0
+        for bad in (2, -1):
+            _, rc, _ = c1.lat.solve(c1_ref[0], tol=1e-10, residual_prec=bad, raise_on_error=False)
+            assert rc == B.QCD_ERR_ARG
     b, x_ref = c1_ref
     x, rc, info = c1.lat.solve(b, tol=1e-10, sap_prec="half", inner_tol=1e-5, residual_prec=residual_prec)
     x = to_np(x)
