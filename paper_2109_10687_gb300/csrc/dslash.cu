@@ -37,7 +37,7 @@ struct Prec<df64> {
   using CB = CloverBlockDF64;
 };
 
-__global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
+__global__ void __launch_bounds__(192, 4) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
                                                                 LinkPtr<df64> U, CloverPtrDF64 clov, df64 kappa,
                                                                 int nrhs);
 
@@ -488,15 +488,20 @@ __device__ __forceinline__ void df_proj(const cx<df64> q[4], cx<df64>& h0, cx<df
   project1<MU, FWD ? -1 : +1>(q[0], q[1], q[2], q[3], h0, h1);
 }
 
-// phase 1: rows (h0, h1) of colour a of the projected neighbour, signed
-__device__ __forceinline__ void df_project(const Geom& g, const DF64Spinor& in, int hop, int dom, int s, int a,
-                                           const int nb[8], int tf, float4* sh, int sl) {
+// phase 1 loads: colour a of the four spins of hop's neighbour, and its sign
+__device__ __forceinline__ void df_project_load(const Geom& g, const DF64Spinor& in, int hop, int dom, int s, int a,
+                                                const int nb[8], int tf, float4 q[4], bool& neg) {
   int nd, ns;
-  bool neg;
   df_nbr(g, hop >> 1, !(hop & 1), dom, s, nb, tf, nd, ns, neg);
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) q[sp] = __ldg(in.p + in.idx(g, nd, sp * 3 + a, ns));
+}
+
+// phase 1: rows (h0, h1) of colour a of the projected neighbour, signed
+__device__ __forceinline__ void df_project(int hop, int a, const float4 qv[4], bool neg, float4* sh, int sl) {
   cx<df64> q[4];
 #pragma unroll
-  for (int sp = 0; sp < 4; ++sp) q[sp] = df_unpack(__ldg(in.p + in.idx(g, nd, sp * 3 + a, ns)));
+  for (int sp = 0; sp < 4; ++sp) q[sp] = df_unpack(qv[sp]);
   cx<df64> h0, h1;
   switch (hop) {
     case 0: df_proj<0, true>(q, h0, h1); break;
@@ -538,25 +543,31 @@ __device__ __forceinline__ void df_rebuild(cx<df64> h0, cx<df64> h1, cx<df64> ac
   }
 }
 
-// phase 2: row a of U h (forward) or U^dag h (backward), rebuilt into colour a
-__device__ __forceinline__ void df_mul_acc(const Geom& g, const LinkPtr<df64>& U, int hop, int dom, int s, int a,
-                                           const int nb[8], int tf, const float4* sh, int sl, cx<df64> acc[4]) {
+// phase 2 loads: row a (forward) or column a (backward) of hop's link
+__device__ __forceinline__ void df_link_load(const Geom& g, const LinkPtr<df64>& U, int hop, int dom, int s, int a,
+                                             const int nb[8], int tf, float4 v[3]) {
   const int mu = hop >> 1;
   const bool fwd = !(hop & 1);
   int nd, ns;
   bool neg;
   df_nbr(g, mu, fwd, dom, s, nb, tf, nd, ns, neg);
-  cx<df64> row[3];
-  {
-    const size_t base = ((size_t)(((fwd ? dom : nd) * 4 + mu) * 9)) << g.logvd;
-    const int site = fwd ? s : ns;
+  const size_t base = ((size_t)(((fwd ? dom : nd) * 4 + mu) * 9)) << g.logvd;
+  const int site = fwd ? s : ns;
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int e = fwd ? a * 3 + b : b * 3 + a;
-      const float4 v = __ldg(U.p + base + ((size_t)e << g.logvd) + site);
-      row[b] = fwd ? make_cx(df64(v.x, v.y), df64(v.z, v.w)) : make_cx(df64(v.x, v.y), -df64(v.z, v.w));
-    }
+  for (int b = 0; b < 3; ++b) {
+    const int e = fwd ? a * 3 + b : b * 3 + a;
+    v[b] = __ldg(U.p + base + ((size_t)e << g.logvd) + site);
   }
+}
+
+// phase 2: row a of U h (forward) or U^dag h (backward), rebuilt into colour a
+__device__ __forceinline__ void df_mul_acc(int hop, const float4 v[3], const float4* sh, int sl, cx<df64> acc[4]) {
+  const bool fwd = !(hop & 1);
+  cx<df64> row[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+    row[b] = fwd ? make_cx(df64(v[b].x, v[b].y), df64(v[b].z, v[b].w))
+                 : make_cx(df64(v[b].x, v[b].y), -df64(v[b].z, v[b].w));
   cx<df64> uh[2];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -579,28 +590,38 @@ __device__ __forceinline__ void df_mul_acc(const Geom& g, const LinkPtr<df64>& U
 
 // (1 + C) x, row i of block b (i = 3 r + a, known at run time): the block's
 // packed reals come straight from memory, the diagonal one as a real
-// factor and the off-diagonal ones conjugated below the diagonal
+// factor and the off-diagonal ones conjugated below the diagonal; the loads
+// of column j + 1 are issued before the arithmetic of column j
+__device__ __forceinline__ float4 df_clover_entry(const float4* cp, int logvd, int i, int j) {
+  const int k = j == i ? (i >> 1) : 3 + (j > i ? herm_off(i, j) : herm_off(j, i));
+  return __ldg(cp + ((size_t)k << logvd));
+}
 __device__ __forceinline__ cx<df64> df_clover_row(const Geom& g, const DF64Spinor& in, const CloverPtrDF64& clov,
                                                   int dom, int s, int b, int i) {
   const float4* cp = clov.p + (((size_t)(dom * 36 + 18 * b)) << g.logvd) + s;
   cx<df64> y = make_cx(df64(0.f), df64(0.f));
+  float4 xn = __ldg(in.p + in.idx(g, dom, (2 * b) * 3, s));
+  float4 cn = df_clover_entry(cp, g.logvd, i, 0);
 #pragma unroll 1
   for (int j = 0; j < 6; ++j) {
-    const cx<df64> xj = df_unpack(__ldg(in.p + in.idx(g, dom, (2 * b + j / 3) * 3 + j % 3, s)));
+    const float4 xv = xn, cv = cn;
+    if (j < 5) {
+      xn = __ldg(in.p + in.idx(g, dom, (2 * b + (j + 1) / 3) * 3 + (j + 1) % 3, s));
+      cn = df_clover_entry(cp, g.logvd, i, j + 1);
+    }
+    const cx<df64> xj = df_unpack(xv);
     if (j == i) {
-      const float4 v = __ldg(cp + ((size_t)(i >> 1) << g.logvd));
-      const df64 d = (i & 1) ? df64(v.z, v.w) : df64(v.x, v.y);
+      const df64 d = (i & 1) ? df64(cv.z, cv.w) : df64(cv.x, cv.y);
       y = make_cx(fma(d, xj.re, y.re), fma(d, xj.im, y.im));
     } else {
-      const int k = j > i ? herm_off(i, j) : herm_off(j, i);
-      const cx<df64> c = df_unpack(__ldg(cp + ((size_t)(3 + k) << g.logvd)));
+      const cx<df64> c = df_unpack(cv);
       y = j > i ? cmac(y, c, xj) : cmacc(y, c, xj);
     }
   }
   return y;
 }
 
-__global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
+__global__ void __launch_bounds__(192, 4) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
                                                                 LinkPtr<df64> U, CloverPtrDF64 clov, df64 kappa,
                                                                 int nrhs) {
   __shared__ float4 sh[8 * 2 * 3 * DF_SITES];  // projected rows [hop][row][colour][site], 48 KB
@@ -624,14 +645,37 @@ __global__ void __launch_bounds__(192) dslash_df64_split_kernel(Geom g, DF64Spin
     nb[4] = n1.x; nb[5] = n1.y; nb[6] = n1.z; nb[7] = n1.w;
   }
   const int tf = __ldg(g.tflag + dom);
+  // each loop issues the next hop's loads before this hop's arithmetic
+  {
+    float4 qn[4];
+    bool negn;
+    df_project_load(g, inr, 0, dom, s, a, nb, tf, qn, negn);
 #pragma unroll 1
-  for (int hop = 0; hop < 8; ++hop) df_project(g, inr, hop, dom, s, a, nb, tf, sh, sl);
+    for (int hop = 0; hop < 8; ++hop) {
+      float4 q[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] = qn[k];
+      const bool neg = negn;
+      if (hop < 7) df_project_load(g, inr, hop + 1, dom, s, a, nb, tf, qn, negn);
+      df_project(hop, a, q, neg, sh, sl);
+    }
+  }
   __syncthreads();
   cx<df64> acc[4];
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) acc[sp] = make_cx(df64(0.f), df64(0.f));
+  {
+    float4 vn[3];
+    df_link_load(g, U, 0, dom, s, a, nb, tf, vn);
 #pragma unroll 1
-  for (int hop = 0; hop < 8; ++hop) df_mul_acc(g, U, hop, dom, s, a, nb, tf, sh, sl, acc);
+    for (int hop = 0; hop < 8; ++hop) {
+      float4 v[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k] = vn[k];
+      if (hop < 7) df_link_load(g, U, hop + 1, dom, s, a, nb, tf, vn);
+      df_mul_acc(hop, v, sh, sl, acc);
+    }
+  }
   if (!live) return;
   // (1 + C) x, rows (block b, spin-in-block r, colour a): index i = 3 r + a
   cx<df64> res[4];
