@@ -378,6 +378,8 @@ def main():
     ap.add_argument("--no-48", action="store_true", help="skip the 48^4 batched comparison")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged 32-lattice batch comparison")
     ap.add_argument("--no-n2", action="store_true", help="skip the paper-parameter (16x6x4x3 domains) rates")
+    ap.add_argument("--no-grad", action="store_true", help="skip the 16^4 and 32^4 gradients")
+    ap.add_argument("--no-64", action="store_true", help="skip the 64^4 operator and solves")
     ap.add_argument("--kernel", choices=["sap16", "sap16g", "sap32", "dslash", "dslash64", "solve_df"], default=None,
                     help="profiling case: set up the workload and run only REPS applications of one kernel")
     ap.add_argument("--lattice", type=int, default=32, help="lattice extent of the profiling case")
@@ -665,6 +667,18 @@ def main():
         # the same lattices as concurrent and as sequential solves
         import bench_configs
         line["ragged_batch_32"] = bench_configs.ragged_batch(reps=3, precs=("half",), dslash=False)
+        barrier()
+    if not args.no_grad:
+        # gradients of Re(eta^dag D^-1 b) with respect to b and U at 16^4 and 32^4
+        import bench_configs
+        g4 = bench_configs.c4(argparse.Namespace(steps=5))
+        line["gradient_16x4_32x4"] = dict(g4["results"], workload=g4["config"]["workload"])
+        barrier()
+    if not args.no_64:
+        # 64^4: the float32 D's GB/s and the mixed against the plain float32 solve
+        import bench_configs
+        g5 = bench_configs.c5(argparse.Namespace(steps=2))
+        line["lattice_64x4"] = dict(g5["results"], workload=g5["config"]["workload"])
         barrier()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(iters={"inner": inner, "outer": outer})
