@@ -690,11 +690,13 @@ __global__ void __launch_bounds__(192, 4) dslash_df64_split_kernel(Geom g, DF64S
   }
 }
 
-// float64 (double2) fields -> double-float (float4) copies, elementwise
+// float64 (double2) fields -> double-float (float4) copies, elementwise, by
+// integer operations on the bits (links and clover entries are far inside
+// float32's range)
 __global__ void f64_to_df64_kernel(const double2* __restrict__ in, float4* out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double2 v = in[i];
-    const df64 re(v.x), im(v.y);
+    const df64 re = df64_from_double_scaled(v.x, 0), im = df64_from_double_scaled(v.y, 0);
     out[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }

@@ -511,62 +511,87 @@ __global__ void k_f64_axpy_f32(Geom g, double2* x, const float4* __restrict__ q,
 // double-float versions of the Algorithm-4 vector kernels (float4 per
 // complex: re.hi, re.lo, im.hi, im.lo; same element order as float64)
 // ---------------------------------------------------------------------------
-// elementwise, in place allowed: float64 -> double-float
-__global__ void k_df_from_f64(const double2* in, float4* out, size_t n2) {
+// A double-float number has the exponent range of float32, so b, x and r
+// are held scaled by a power of two 2^k (exact), with k chosen from |b|^2
+// (b2, computed in float64) so that b's components are of order one; the
+// residual norms are reported unscaled.  D is linear, so the scaled system
+// has the same solution, scaled.
+__device__ __forceinline__ int df_scale_exp(const double* b2, int rhs, size_t n2) {
+  int e = 0;
+  const double m = b2[rhs] / (double)n2;
+  if (m > 0.0) frexp(m, &e);
+  return max(-120, min(120, -e / 2));
+}
+// float64 -> scaled double-float, one right-hand side per grid row; in
+// place allowed (the conversions are integer operations on the bits)
+__global__ void k_df_from_f64(const double2* in, float4* out, size_t n2, const double* b2) {
+  const int rhs = blockIdx.y;
+  const int k = df_scale_exp(b2, rhs, n2);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
-    const double2 v = in[i];
-    const df64 re(v.x), im(v.y);
-    out[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    const double2 v = in[rhs * n2 + i];
+    const df64 re = df64_from_double_scaled(v.x, k), im = df64_from_double_scaled(v.y, k);
+    out[rhs * n2 + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
-// elementwise, in place allowed: double-float -> float64
-__global__ void k_f64_from_df(const float4* in, double2* out, size_t n2) {
+// scaled double-float -> float64, in place allowed
+__global__ void k_f64_from_df(const float4* in, double2* out, size_t n2, const double* b2) {
+  const int rhs = blockIdx.y;
+  const int k = df_scale_exp(b2, rhs, n2);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 v = in[i];
-    out[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    const float4 v = in[rhs * n2 + i];
+    out[rhs * n2 + i] =
+        make_double2(df64_to_double_scaled(df64(v.x, v.y), k), df64_to_double_scaled(df64(v.z, v.w), k));
   }
 }
-// r = b - r (r holds D x on entry), in double-float; out[rhs] = |r|^2 (float64 sums)
-__global__ void k_residual_df(const float4* __restrict__ b, float4* r, size_t n2, double* out, double* partials,
-                              unsigned* counters) {
+// r = b - r (r holds D x on entry), in double-float; out[rhs] = |r|^2,
+// unscaled.  The arithmetic stays on the float32 pipes (the float64 pipe of
+// this GPU is a small fraction of their width): squares of each component's
+// high part (the scaled components are of order one, their squares well
+// inside the float32 range), float32 sums over each thread's elements
+// (relative error about 1e-6, far below what the stopping test at 1e-10
+// and the reported residual need), float64 across threads.
+__global__ void k_residual_df(const float4* __restrict__ b, float4* r, size_t n2, const double* b2, double* out,
+                              double* partials, unsigned* counters) {
   const int rhs = blockIdx.y;
   const size_t off = (size_t)rhs * n2;
   double* part = partials + (size_t)rhs * MAX_RED_OUT * gridDim.x;
-  double s = 0.0;
+  const int k = df_scale_exp(b2, rhs, n2);
+  float s = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
     const float4 bv = b[off + i], dv = r[off + i];
     const df64 re = df64(bv.x, bv.y) - df64(dv.x, dv.y);
     const df64 im = df64(bv.z, bv.w) - df64(dv.z, dv.w);
     r[off + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
-    const double dr = to_double(re), di = to_double(im);
-    s = fma(dr, dr, fma(di, di, s));
+    s = fmaf(re.hi, re.hi, fmaf(im.hi, im.hi, s));
   }
-  double v[1] = {s}, tot[1];
+  double v[1] = {ldexp((double)s, -2 * k)}, tot[1];
   if (grid_reduce<1>(v, part, counters + rhs, tot) && threadIdx.x == 0) out[rhs] = tot[0];
 }
-// float32 p = R_SP(r / err) from a double-float r
-__global__ void k_df_to_f32_scaled(Geom g, const float4* __restrict__ r, float4* p, const double* scale) {
+// float32 p = R_SP(r / err) from the scaled double-float r (err unscaled),
+// in float32 arithmetic: (hi + lo) f as hi f + lo f with one rounding
+__global__ void k_df_to_f32_scaled(Geom g, const float4* __restrict__ r, float4* p, const double* scale,
+                                   const double* b2) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= g.vol) return;
   const int rhs = blockIdx.y;
   const int dom = (int)(gid >> g.logvd) + rhs * g.ndom, s = (int)(gid & (g.vd - 1));
-  const double f = scale[rhs];
+  const float f = (float)ldexp(scale[rhs], -df_scale_exp(b2, rhs, (size_t)g.vol * 12));
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const float4 a = r[((size_t)(dom * 12 + 2 * k) << g.logvd) + s];
     const float4 b = r[((size_t)(dom * 12 + 2 * k + 1) << g.logvd) + s];
-    p[((size_t)(dom * 6 + k) << g.logvd) + s] =
-        make_float4((float)(((double)a.x + a.y) * f), (float)(((double)a.z + a.w) * f),
-                    (float)(((double)b.x + b.y) * f), (float)(((double)b.z + b.w) * f));
+    p[((size_t)(dom * 6 + k) << g.logvd) + s] = make_float4(fmaf(a.x, f, a.y * f), fmaf(a.z, f, a.w * f),
+                                                            fmaf(b.x, f, b.y * f), fmaf(b.z, f, b.w * f));
   }
 }
-// double-float x += err * P_DP(q32)
-__global__ void k_df_axpy_f32(Geom g, float4* x, const float4* __restrict__ q, const double* scale) {
+// scaled double-float x += err * P_DP(q32) (err unscaled)
+__global__ void k_df_axpy_f32(Geom g, float4* x, const float4* __restrict__ q, const double* scale,
+                              const double* b2) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= g.vol) return;
   const int rhs = blockIdx.y;
   const int dom = (int)(gid >> g.logvd) + rhs * g.ndom, s = (int)(gid & (g.vd - 1));
-  const df64 f(scale[rhs]);
+  const df64 f(ldexp(scale[rhs], df_scale_exp(b2, rhs, (size_t)g.vol * 12)));
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const float4 v = q[((size_t)(dom * 6 + k) << g.logvd) + s];
@@ -999,10 +1024,9 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   float4* bdf = reinterpret_cast<float4*>(w->t64);
   float4* xdf = reinterpret_cast<float4*>(w->x64);
   float4* rdf = reinterpret_cast<float4*>(w->r64);
-  const size_t n2all = n2 * nrhs;
   if (df) {
     LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-    k_df_from_f64<<<1024, 256, 0, st>>>(w->b64, bdf, n2all);
+    k_df_from_f64<<<dim3(1024, nrhs), 256, 0, st>>>(w->b64, bdf, n2, d_red);
     check_launch();
   }
   if (P.x_is_guess) {
@@ -1010,7 +1034,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     if (rc != QCD_OK) throw Error{rc, ctx->err};
     if (df) {
       LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-      k_df_from_f64<<<1024, 256, 0, st>>>(w->x64, xdf, n2all);
+      k_df_from_f64<<<dim3(1024, nrhs), 256, 0, st>>>(w->x64, xdf, n2, d_red);
       check_launch();
     }
   } else {
@@ -1023,7 +1047,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     if (df) {
       dslash_launch(ctx, rdf, xdf, PREC_DF64, MODE_D, nrhs, st);
       LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-      k_residual_df<<<rgrid, RED_THREADS, 0, st>>>(bdf, rdf, n2, d_red + nrhs, w->partials, w->counters);
+      k_residual_df<<<rgrid, RED_THREADS, 0, st>>>(bdf, rdf, n2, d_red, d_red + nrhs, w->partials, w->counters);
       check_launch();
     } else {
       dslash_launch(ctx, w->r64, w->x64, QCD_PREC_DOUBLE, MODE_D, nrhs, st);
@@ -1224,7 +1248,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     {
       LaunchScope ls(ctx, QCD_KC_BLAS, st);
-      if (df) k_df_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, rdf, w->tmp32, d_red + 2 * nrhs);
+      if (df) k_df_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, rdf, w->tmp32, d_red + 2 * nrhs, d_red);
       else k_f64_to_f32_scaled<<<sgrid, 128, 0, st>>>(g, w->r64, w->tmp32, d_red + 2 * nrhs);
       check_launch();
     }
@@ -1248,7 +1272,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
     QCD_CUDA_CHECK(cudaMemcpyAsync(d_red + 2 * nrhs, h_scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     {
       LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-      if (df) k_df_axpy_f32<<<sgrid, 128, 0, st>>>(g, xdf, w->x, d_red + 2 * nrhs);
+      if (df) k_df_axpy_f32<<<sgrid, 128, 0, st>>>(g, xdf, w->x, d_red + 2 * nrhs, d_red);
       else k_f64_axpy_f32<<<sgrid, 128, 0, st>>>(g, w->x64, w->x, d_red + 2 * nrhs);
       check_launch();
     }
@@ -1257,7 +1281,7 @@ extern "C" int qcd_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, int
   }
   if (df) {
     LaunchScope ls(ctx, QCD_KC_DOUBLE, st);
-    k_f64_from_df<<<1024, 256, 0, st>>>(xdf, w->x64, n2all);
+    k_f64_from_df<<<dim3(1024, nrhs), 256, 0, st>>>(xdf, w->x64, n2, d_red);
     check_launch();
   }
   rc = qcd_export_spinor(ctx, x, w->x64, QCD_PREC_DOUBLE, nrhs, on_device, stream);

@@ -95,6 +95,24 @@ def test_double_float_residual_bound(kappa, seed):
         p.close()
 
 
+@pytest.mark.parametrize("factor", [1e-30, 1e25])
+def test_double_float_residual_far_from_unit_sources(c1, c1_ref, factor):
+    """The double-float residual (the default) keeps b, x and r scaled by a
+    power of two that brings b's components to order one, so sources far
+    outside float32's comfortable range solve as well: b times 1e-30 (whose
+    residual at 1e-10 would be below float32's smallest normal number) and
+    times 1e25.  x scales with b exactly; the oracle's residual of x is below
+    1e-10 and agrees with the reported one."""
+    b, x_ref = c1_ref
+    bs = b * factor
+    x, rc, info = c1.lat.solve(bs, tol=1e-10, sap_prec="half", inner_tol=1e-5)
+    x = to_np(x)
+    assert rc == 0
+    r = true_resid(c1.op, x, bs)
+    assert r < 1e-10 and abs(info.true_resid - r) <= 1e-12, (r, info.true_resid)
+    assert rel_l2(x / factor, x_ref) < 1e-8
+
+
 @pytest.mark.parametrize("use_graph", [0, 2])
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, -1])
 def test_solve_with_each_sap_kernel_shape(c1, c1_ref, shape, use_graph):
