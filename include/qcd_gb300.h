@@ -134,8 +134,10 @@ int qcd_create(const int dims[4], const int domain[4], int bc_t, int basis, qcd_
 /* Free every device buffer the context owns, then the context. */
 int qcd_destroy(qcd_ctx* ctx);
 
-/* Message of the last failing call on ctx (or of the last qcd_create when
- * ctx is NULL).  The string is owned by the library. */
+/* Message of the last failing call on ctx (or, when ctx is NULL, of the
+ * calling thread's last failing qcd_create).  The string is owned by the
+ * library and stays valid until the next failing call on ctx (or the
+ * thread's next failing qcd_create). */
 const char* qcd_last_error(const qcd_ctx* ctx);
 
 /* Library version string, e.g. "qcd_gb300 1.0". */

@@ -252,7 +252,7 @@ using namespace qcd;
 // ---------------------------------------------------------------------------
 // C entry points
 // ---------------------------------------------------------------------------
-static std::string g_create_error;
+static thread_local std::string g_create_error;  // per calling thread
 
 #define QCD_API_BEGIN(ctx) \
   try {

@@ -1045,17 +1045,18 @@ static void flow_sequence(qcd_ctx* ctx, F32Spinor s_first_in32, SIO s, SIO x, F3
   f.ctr = ctx->flow_state;
   f.n_sap = n_sap;
   f.stagger_ns = stagger_ns;
-  // every CTA of the grid must be resident at once: as many as fit
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
+  // as many CTAs as can be resident at once (computed once; the batch
+  // solve's host threads may get here together)
+  static const int resident = [] {
+    int dev = 0, sms = 0, per_sm = 0;
     QCD_CUDA_CHECK(cudaGetDevice(&dev));
     QCD_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     QCD_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sap_flow_kernel<HALF, SIO>, ST_THREADS,
                                                                  st_smem_bytes<HALF>()));
-  }
+    return per_sm * sms;
+  }();
   const int total = 2 * (n_sap + 1) * ctx->geom.nhalf;
-  const int grid = std::max(1, std::min(total, per_sm * sms));
+  const int grid = std::max(1, std::min(total, resident));
   LaunchScope ls(ctx, QCD_KC_SAP_BLOCK, st);
   launch_pdl(sap_flow_kernel<HALF, SIO>, dim3(grid), dim3(ST_THREADS), st_smem_bytes<HALF>(), st, a, f);
   check_launch();
