@@ -101,8 +101,9 @@ typedef struct qcd_solve_params {
                           stops on is within 2^-48 (1 + 300 |x| / |b|) of
                           the float64 residual of the same x), 1 native
                           float64; other values QCD_ERR_ARG.  The flexible
-                          GMRES outer iteration and the shared-launch batch
-                          solve compute in native float64 either way.       */
+                          GMRES outer iteration computes in native float64
+                          either way; the shared-launch batch solve keeps x,
+                          r and b in float64 and computes D x as selected.  */
   int outer_restart;   /* outer iteration: 0 (default) the defect correction
                           of Algorithm 4; m >= 1 flexible GMRES with restart
                           length m, in float64, each inner SAP-BiCGStab
@@ -309,8 +310,8 @@ int qcd_batch_apply_D(qcd_batch* batch, void* const* out, const void* const* in,
  * float64 fields as in qcd_solve; Algorithm 4 around Algorithm 5 on
  * A M_SAP, Sec. 3).  When every lattice has 4^4 domains (and no SAP domains
  * of its own, see qcd_set_sap_domain) and outer_restart = 0, the lattices
- * are solved in SHARED LAUNCHES (with the residual in native float64 for
- * either residual_prec): each
+ * are solved in SHARED LAUNCHES (x, r and b in float64; D x of the
+ * residual in double-float for residual_prec 0, in float64 for 1): each
  * SAP half-sweep (Algorithm 1), each application of A and of the float64 D,
  * and each fused BLAS-1 step of Algorithm 5 is one kernel launch over every
  * lattice, through work lists built on the first call; the inner loop is one

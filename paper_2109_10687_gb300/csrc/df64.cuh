@@ -70,6 +70,17 @@ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) {
   return quick_two_sum(s.hi, s.lo);
 }
 
+// The exponent k of the power of two 2^k that brings a field with |b|^2 =
+// b2 over n2 complex components to components of order one: the
+// double-float paths hold b, x and r scaled by it, since a double-float
+// number has the exponent range of float32 (k = 0 for a zero field).
+__device__ __forceinline__ int df_scale_exp(double b2, size_t n2) {
+  int e = 0;
+  const double m = b2 / (double)n2;
+  if (m > 0.0) frexp(m, &e);
+  return max(-120, min(120, -e / 2));
+}
+
 // Conversions between float64 and double-float with a power-of-two scale
 // 2^k folded in, by integer operations on the IEEE-754 bit fields (sign,
 // biased exponent, significand) instead of float64 arithmetic: the

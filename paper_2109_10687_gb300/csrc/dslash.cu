@@ -621,22 +621,22 @@ __device__ __forceinline__ cx<df64> df_clover_row(const Geom& g, const DF64Spino
   return y;
 }
 
-__global__ void __launch_bounds__(192, 4) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
-                                                                LinkPtr<df64> U, CloverPtrDF64 clov, df64 kappa,
-                                                                int nrhs) {
-  __shared__ float4 sh[8 * 2 * 3 * DF_SITES];  // projected rows [hop][row][colour][site], 48 KB
+// One tile of DF_SITES sites from site0 (lexicographic-domain order) of the
+// field `in` (one right-hand side); every thread of the block takes part.
+// store(dom, comp, s, value) writes one colour row of the result.
+template <typename Store>
+__device__ __forceinline__ void df64_tile(const Geom& g, const DF64Spinor& inr, const LinkPtr<df64>& U,
+                                          const CloverPtrDF64& clov, df64 kappa, long long site0, float4* sh,
+                                          const Store& store) {
   const int a = threadIdx.y;  // colour row
   const int sl = threadIdx.z * 32 + threadIdx.x;
-  const int rhs = blockIdx.x % nrhs;
-  const long long gid = (blockIdx.x / nrhs) * (long long)DF_SITES + sl;
+  const long long gid = site0 + sl;
   // every thread takes part in the barrier; sites past the end compute on
   // site 0 of the block's range and store nothing
   const bool live = gid < g.vol;
-  const long long gq = live ? gid : (blockIdx.x / nrhs) * (long long)DF_SITES;
+  const long long gq = live ? gid : site0;
   const int dom = __ldg(g.lex2dom + (int)(gq >> g.logvd));
   const int s = (int)(gq & (g.vd - 1));
-  const int rhs_off = rhs * g.ndom;
-  const DF64Spinor inr{in.p + ((size_t)rhs_off * 12 << g.logvd)};
   int nb[8];
   {
     const int4 n0 = __ldg(reinterpret_cast<const int4*>(g.nbr) + 2 * dom);
@@ -684,10 +684,60 @@ __global__ void __launch_bounds__(192, 4) dslash_df64_split_kernel(Geom g, DF64S
 #pragma unroll
     for (int r = 0; r < 2; ++r) res[2 * b + r] = df_clover_row(g, inr, clov, dom, s, b, 3 * r + a);
 #pragma unroll
-  for (int sp = 0; sp < 4; ++sp) {
-    const cx<df64> o = make_cx(fma(-kappa, acc[sp].re, res[sp].re), fma(-kappa, acc[sp].im, res[sp].im));
-    out.p[out.idx(g, dom + rhs_off, sp * 3 + a, s)] = df_pack(o);
+  for (int sp = 0; sp < 4; ++sp)
+    store(dom, sp * 3 + a, s, make_cx(fma(-kappa, acc[sp].re, res[sp].re), fma(-kappa, acc[sp].im, res[sp].im)));
+}
+
+__global__ void __launch_bounds__(192, 4) dslash_df64_split_kernel(Geom g, DF64Spinor out, DF64Spinor in,
+                                                                LinkPtr<df64> U, CloverPtrDF64 clov, df64 kappa,
+                                                                int nrhs) {
+  __shared__ float4 sh[8 * 2 * 3 * DF_SITES];  // projected rows [hop][row][colour][site], 48 KB
+  const int rhs = blockIdx.x % nrhs;
+  const int rhs_off = rhs * g.ndom;
+  const DF64Spinor inr{in.p + ((size_t)rhs_off * 12 << g.logvd)};
+  df64_tile(g, inr, U, clov, kappa, (blockIdx.x / nrhs) * (long long)DF_SITES, sh,
+            [&](int dom, int comp, int s, cx<df64> o) { out.p[out.idx(g, dom + rhs_off, comp, s)] = df_pack(o); });
+}
+
+// Ragged batch: the double-float D of Algorithm 4 (r64 = D x, read from the
+// scaled double-float copy xdf, written to float64 unscaled) over every
+// lattice in one launch.  Tile b of DF_SITES sites belongs to lattice
+// tile_lat[b]; the lattice's descriptor is copied to shared memory.
+__global__ void __launch_bounds__(192, 4) lat_dslash_df64_kernel(const LatDesc* __restrict__ desc,
+                                                                const int* __restrict__ tile_lat,
+                                                                const double* __restrict__ b2) {
+  extern __shared__ float4 dsh[];  // projected rows, 48 KB, then the descriptor
+  LatDesc& sd = *reinterpret_cast<LatDesc*>(dsh + 8 * 2 * 3 * DF_SITES);
+  const int lat = __ldg(tile_lat + blockIdx.x);
+  {
+    const int* src = reinterpret_cast<const int*>(desc + lat);
+    int* dst = reinterpret_cast<int*>(&sd);
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    const int t = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    for (int k = t; k < (int)(sizeof(LatDesc) / sizeof(int)); k += nt) dst[k] = __ldg(src + k);
   }
+  __syncthreads();
+  const int kexp = df_scale_exp(b2[lat], (size_t)sd.g.vol * 12);
+  const F64Spinor out{sd.r64};
+  const Geom& g = sd.g;
+  df64_tile(g, DF64Spinor{sd.xdf}, LinkPtr<df64>{sd.udf}, CloverPtrDF64{sd.clovdf}, df64(sd.kappa64),
+            ((long long)blockIdx.x - sd.df_tile_begin) * DF_SITES, dsh, [&](int dom, int comp, int s, cx<df64> o) {
+              out.p[out.idx(g, dom, comp, s)] =
+                  make_double2(df64_to_double_scaled(o.re, kexp), df64_to_double_scaled(o.im, kexp));
+            });
+}
+
+void lat_dslash_df64_launch(const LatDesc* d_lat, const int* d_tile_lat, long long tiles, const double* d_b2,
+                            cudaStream_t st) {
+  QCD_REQUIRE(tiles < (1LL << 31), QCD_ERR_ARG, "batch too large for one launch");
+  const int smem = (int)(sizeof(float4) * 8 * 2 * 3 * DF_SITES + sizeof(LatDesc));
+  static const bool attr = [smem] {
+    QCD_CUDA_CHECK(cudaFuncSetAttribute(lat_dslash_df64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return true;
+  }();
+  (void)attr;
+  lat_dslash_df64_kernel<<<(unsigned)tiles, dim3(32, 3, 2), smem, st>>>(d_lat, d_tile_lat, d_b2);
+  check_launch();
 }
 
 // float64 (double2) fields -> double-float (float4) copies, elementwise, by

@@ -807,12 +807,20 @@ struct LatDesc {
   const double2* clov64;
   float4 *x, *q, *t, *zp, *zr, *b32;   // float32 internal fields of Algorithm 5
   double2 *x64, *r64, *b64;            // float64 internal fields of Algorithm 4
+  const float4* udf;                   // links and 1 + C in double-float
+  const float4* clovdf;
+  float4* xdf;                         // scaled double-float copy of x64
   const int* done;                     // this lattice's BiCGStab stop flag
   long long block_begin;               // first 128-thread block of this lattice
+  long long df_tile_begin;             // first 64-site double-float tile of this lattice
 };
 // which: 0 q = A zp, 1 t = A zr (float32; lattices whose done flag is set
 // are skipped), 2 r64 = D x64 (float64)
 void lat_dslash_launch(const LatDesc* d_lat, const int* d_block_lat, long long blocks, int which, cudaStream_t st);
+// r64 = D x of every lattice in double-float, from the copy xdf scaled by
+// the power of two of its lattice's |b|^2 (b2), written unscaled in float64
+void lat_dslash_df64_launch(const LatDesc* d_lat, const int* d_tile_lat, long long tiles, const double* d_b2,
+                            cudaStream_t st);
 
 // M_SAP (Algorithm 1) of every lattice of a ragged batch in shared launches:
 // one launch per half-sweep covers every lattice's domains of that colour.

@@ -39,6 +39,7 @@ struct RaggedWS {
   float4 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *t = nullptr, *zp = nullptr, *zr = nullptr,
          *rt = nullptr, *b32 = nullptr, *sap_s = nullptr, *halo = nullptr;
   double2 *x64 = nullptr, *r64 = nullptr, *b64 = nullptr;
+  float4* xdf = nullptr;   // scaled double-float copy of x64 (residual_prec 0)
   double* partials = nullptr;
   unsigned* counters = nullptr;
   Scal* scal = nullptr;
@@ -52,6 +53,8 @@ struct RaggedWS {
   LatDesc* d_lat = nullptr;
   int* d_site_lat = nullptr;
   long long site_blocks = 0;
+  int* d_tile_lat = nullptr;  // lattice of every 64-site double-float tile
+  long long df_tiles = 0;
   SapBatchPlan* plan_p = nullptr;  // M_SAP p -> zp
   SapBatchPlan* plan_r = nullptr;  // M_SAP r -> zr
   int plan_prec = -1, plan_nsap = -1, plan_njac = -1;
@@ -65,7 +68,7 @@ void ragged_free(RaggedWS* w) {
   if (!w) return;
   void* ptrs[] = {w->d_v4off, w->d_v4len, w->d_n2off, w->d_n2len, w->x, w->r, w->p, w->q, w->t, w->zp, w->zr,
                   w->rt, w->b32, w->sap_s, w->halo, w->x64, w->r64, w->b64, w->partials, w->counters, w->scal,
-                  w->ctrl, w->dres, w->d_status, w->d_lat, w->d_site_lat};
+                  w->ctrl, w->dres, w->d_status, w->d_lat, w->d_site_lat, w->xdf, w->d_tile_lat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (w->h_scal) cudaFreeHost(w->h_scal);
@@ -118,6 +121,18 @@ __global__ void k_rg_residual_f64(const double2* __restrict__ b, double2* r, Seg
   double v[1] = {s}, tot[1];
   if (grid_reduce<1>(v, partials + (size_t)k * MAX_RED_OUT * gridDim.x, counters + k, tot) && threadIdx.x == 0)
     out[k] = tot[0];
+}
+
+// xdf_k = x64_k 2^e_k in double-float, e_k from lattice k's |b|^2 (b2)
+__global__ void k_rg_to_df(const double2* __restrict__ x, float4* xdf, Seg seg, const double* b2) {
+  const int k = blockIdx.y;
+  const size_t off = seg.at(k), n = seg.size(k);
+  const int e = df_scale_exp(b2[k], n);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = x[off + i];
+    const df64 re = df64_from_double_scaled(v.x, e), im = df64_from_double_scaled(v.y, e);
+    xdf[off + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
 }
 
 __device__ __forceinline__ bool rg_site(const LatDesc* __restrict__ desc, const int* __restrict__ site_lat,
@@ -197,7 +212,7 @@ static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
     const int n = (int)ctx.size();
     w->n = n;
     std::vector<LatDesc> lat(n);
-    std::vector<int> site_lat;
+    std::vector<int> site_lat, tile_lat;
     for (int i = 0; i < n; ++i) {
       const Geom& g = ctx[i]->geom;
       w->voff.push_back(w->vtot);
@@ -210,8 +225,11 @@ static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
       w->n2tot += (size_t)g.vol * 12;
       lat[i].block_begin = (long long)site_lat.size();
       for (long long b = 0; b < (g.vol + 127) / 128; ++b) site_lat.push_back(i);
+      lat[i].df_tile_begin = (long long)tile_lat.size();
+      for (long long b = 0; b < (g.vol + 63) / 64; ++b) tile_lat.push_back(i);
     }
     w->site_blocks = (long long)site_lat.size();
+    w->df_tiles = (long long)tile_lat.size();
     auto upload = [](size_t** d, const std::vector<size_t>& h) {
       QCD_CUDA_CHECK(cudaMalloc(d, sizeof(size_t) * h.size()));
       QCD_CUDA_CHECK(cudaMemcpy(*d, h.data(), sizeof(size_t) * h.size(), cudaMemcpyHostToDevice));
@@ -224,6 +242,7 @@ static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
     for (auto v : v32) QCD_CUDA_CHECK(cudaMalloc(v, sizeof(float4) * w->v4tot));
     double2** v64[] = {&w->x64, &w->r64, &w->b64};
     for (auto v : v64) QCD_CUDA_CHECK(cudaMalloc(v, sizeof(double2) * w->n2tot));
+    QCD_CUDA_CHECK(cudaMalloc(&w->xdf, sizeof(float4) * w->n2tot));
     int dev = 0, sms = 0;
     QCD_CUDA_CHECK(cudaGetDevice(&dev));
     QCD_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -262,12 +281,17 @@ static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
       d.x64 = w->x64 + w->n2off[i];
       d.r64 = w->r64 + w->n2off[i];
       d.b64 = w->b64 + w->n2off[i];
+      d.udf = c->udf;
+      d.clovdf = c->clovdf;
+      d.xdf = w->xdf + w->n2off[i];
       d.done = &w->scal[i].done;
     }
     QCD_CUDA_CHECK(cudaMalloc(&w->d_lat, sizeof(LatDesc) * n));
     QCD_CUDA_CHECK(cudaMemcpy(w->d_lat, lat.data(), sizeof(LatDesc) * n, cudaMemcpyHostToDevice));
     QCD_CUDA_CHECK(cudaMalloc(&w->d_site_lat, sizeof(int) * site_lat.size()));
     QCD_CUDA_CHECK(cudaMemcpy(w->d_site_lat, site_lat.data(), sizeof(int) * site_lat.size(), cudaMemcpyHostToDevice));
+    QCD_CUDA_CHECK(cudaMalloc(&w->d_tile_lat, sizeof(int) * tile_lat.size()));
+    QCD_CUDA_CHECK(cudaMemcpy(w->d_tile_lat, tile_lat.data(), sizeof(int) * tile_lat.size(), cudaMemcpyHostToDevice));
     QCD_CUDA_CHECK(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
     for (const qcd_ctx* c : ctx) w->clover_gen.push_back(c->clover_gen);
   } catch (...) {
@@ -444,8 +468,16 @@ int ragged_solve(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp, double* const*
     k_rg_norm2_f64<<<rgrid, RED_THREADS, 0, st>>>(w->b64, seg64, w->dres, w->partials, w->counters);
     check_launch();
   }
+  // D x in double-float (residual_prec 0: from a copy of x scaled by the
+  // power of two of each lattice's |b|^2, written back to float64) or in
+  // float64; x, r and b stay float64 either way
   auto residual = [&]() {
-    {
+    if (P.residual_prec == 0) {
+      LaunchScope ls(c0, QCD_KC_DOUBLE, st);
+      k_rg_to_df<<<rgrid, 256, 0, st>>>(w->x64, w->xdf, seg64, w->dres);
+      check_launch();
+      lat_dslash_df64_launch(w->d_lat, w->d_tile_lat, w->df_tiles, w->dres, st);
+    } else {
       LaunchScope ls(c0, QCD_KC_DOUBLE, st);
       lat_dslash_launch(w->d_lat, w->d_site_lat, w->site_blocks, 2, st);
     }

@@ -516,12 +516,7 @@ __global__ void k_f64_axpy_f32(Geom g, double2* x, const float4* __restrict__ q,
 // (b2, computed in float64) so that b's components are of order one; the
 // residual norms are reported unscaled.  D is linear, so the scaled system
 // has the same solution, scaled.
-__device__ __forceinline__ int df_scale_exp(const double* b2, int rhs, size_t n2) {
-  int e = 0;
-  const double m = b2[rhs] / (double)n2;
-  if (m > 0.0) frexp(m, &e);
-  return max(-120, min(120, -e / 2));
-}
+__device__ __forceinline__ int df_scale_exp(const double* b2, int rhs, size_t n2) { return df_scale_exp(b2[rhs], n2); }
 // float64 -> scaled double-float, one right-hand side per grid row; in
 // place allowed (the conversions are integer operations on the bits)
 __global__ void k_df_from_f64(const double2* in, float4* out, size_t n2, const double* b2) {

@@ -200,3 +200,36 @@ def test_paper_domains_full_size(sap_prec, shape):
         assert np.sqrt(num / den) < 1e-8
     finally:
         lat.close()
+
+
+@pytest.mark.parametrize("sap_prec", ["half", "single"])
+def test_one_launch_msap_at_32x4_equals_per_launch(sap_prec):
+    """At the benchmark's 32^4 size (4096 domains, 2048 per colour), M_SAP in
+    one launch (shape 3: every resident CTA in flight, items ordered by the
+    neighbours' flags) equals the per-launch form (shape 0) bit for bit, for
+    one and for two right-hand sides, twice in a row (the flags and counters
+    are cleared between uses)."""
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300.lattice import Lattice
+    dims = (32, 32, 32, 32)
+    lat = Lattice(dims, (4, 4, 4, 4), -1, "chiral").setup(random_su3_field_fast(dims, 0.3, 1001), 0.125, 1.0)
+    try:
+        prec = {"half": B.PREC_HALF, "single": B.PREC_SINGLE}[sap_prec]
+        b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2001))).cuda().contiguous()
+        outs = {}
+        for nrhs in (1, 2):
+            a = lat.field("single", nrhs)
+            src = b if nrhs == 1 else torch.stack([b, 0.5 * b.roll(1, 0)]).contiguous()
+            B.qcd_import_spinor(lat.ctx, a, src, B.PREC_SINGLE, nrhs)
+            for shape in (0, 3, 3):
+                B.qcd_set_sap_shape(lat.ctx, shape)
+                o = lat.field("single", nrhs)
+                B.qcd_sap_apply_nrhs(lat.ctx, o, a, nrhs, 4, 4, prec, 0)
+                outs.setdefault(nrhs, []).append(o.clone())
+            assert B.qcd_device_status(lat.ctx) == B.QCD_OK
+        for nrhs, (ref, *rest) in outs.items():
+            for o in rest:
+                assert torch.equal(o, ref), nrhs
+    finally:
+        B.qcd_set_sap_shape(lat.ctx, -1)
+        lat.close()
