@@ -353,7 +353,16 @@ def _paper_flop_per_site_iter(domain, n_sap, n_jac, hops=(168, 168, 168, 168)):
     return 2 * (n_sap + 1) * (f_in + n_jac * (f_in + 48) + f_out) + 96 * n_sap + 48 + 1008
 
 
-def _n2_rate(lat, dims, prec, flop, flop_paper_basis=None, n_sap=4, n_jac=2):
+# One A64FX node's site-iterations per second for the paper's SAP domain
+# shapes: Table 2 times 500 iterations on a process block of two domains
+# (the block's extent in x is twice the domain's); a node runs 4 processes.
+def _a64fx_node_rate(domain):
+    table2 = {(16, 6, 4, 3): 0.334867, (16, 6, 4, 6): 0.515010}  # seconds for 500 iterations
+    block_sites = 2 * int(np.prod(domain))
+    return 4 * block_sites * 500 / table2[domain]
+
+
+def _n2_rate(lat, dims, prec, flop, flop_paper_basis=None, n_sap=4, n_jac=2, node_rate=1.38e7):
     """ms per BiCGStab iteration from the difference of two fixed-length solves
     (10 and 30 iterations, one outer step, graph loop)."""
     from lattice_inputs import gaussian_spinor
@@ -374,7 +383,7 @@ def _n2_rate(lat, dims, prec, flop, flop_paper_basis=None, n_sap=4, n_jac=2):
     r = {"lattice": list(dims), "ms_per_iteration": 1e3 * t_iter, "iterations": [i1, i2],
          "site_iterations_per_s": vol / t_iter, "flop_per_site_iteration": flop,
          "tflops_paper_accounting": flop * vol / t_iter / 1e12,
-         "vs_a64fx_node_site_iterations": vol / t_iter / 1.38e7}
+         "a64fx_node_site_iterations_per_s": node_rate, "vs_a64fx_node_site_iterations": vol / t_iter / node_rate}
     if flop_paper_basis is not None:
         r["flop_per_site_iteration_paper_basis"] = flop_paper_basis
         r["tflops_paper_accounting_paper_basis"] = flop_paper_basis * vol / t_iter / 1e12
@@ -384,8 +393,9 @@ def _n2_rate(lat, dims, prec, flop, flop_paper_basis=None, n_sap=4, n_jac=2):
 def n2_paper_domains(float32=True):
     """The paper's parameters (n_sap 4, n_jac 2) on 64x24x32x24 with its own
     16x6x4x3 SAP domains (float16 links and C_inv on the cluster kernel; and
-    float32 on the one-CTA kernel) and with 4^4 domains, against one A64FX
-    node's 1.38e7 site-iterations/s (Table 2, first row)."""
+    float32 on the one-CTA kernel), its 16x6x4x6 domains and 4^4 domains,
+    against one A64FX node (Table 2's row for the same domains; 4^4 against
+    its first row, 1.38e7 site-iterations/s)."""
     from paper_2109_10687_gb300 import binding as B
     n_sap, n_jac = 4, 2
     out = {}
@@ -398,9 +408,17 @@ def n2_paper_domains(float32=True):
     # paper's basis (156 for a temporal hop), which reproduces Tables 2-3
     fl, fl_paper = (_paper_flop_per_site_iter(paper, n_sap, n_jac),
                     _paper_flop_per_site_iter(paper, n_sap, n_jac, hops=(168, 168, 168, 156)))
-    out["float16_gauge_domains_16x6x4x3"] = _n2_rate(lat, dims, "half_gauge", fl, fl_paper)
+    out["float16_gauge_domains_16x6x4x3"] = _n2_rate(lat, dims, "half_gauge", fl, fl_paper,
+                                                     node_rate=_a64fx_node_rate(paper))
     if float32:
-        out["float32_domains_16x6x4x3"] = _n2_rate(lat, dims, "single", fl, fl_paper)
+        out["float32_domains_16x6x4x3"] = _n2_rate(lat, dims, "single", fl, fl_paper,
+                                                   node_rate=_a64fx_node_rate(paper))
+    # Table 2's fastest row: 16x6x4x6 domains (six time slices per cluster)
+    paper6 = (16, 6, 4, 6)
+    B.qcd_set_sap_domain(lat.ctx, paper6)
+    out["float16_gauge_domains_16x6x4x6"] = _n2_rate(
+        lat, dims, "half_gauge", _paper_flop_per_site_iter(paper6, n_sap, n_jac),
+        _paper_flop_per_site_iter(paper6, n_sap, n_jac, hops=(168, 168, 168, 156)), node_rate=_a64fx_node_rate(paper6))
     out["tuning"] = [ln for ln in B.qcd_tuning_report(lat.ctx).splitlines() if ln.startswith("sap_general")]
     lat.close()
     return out

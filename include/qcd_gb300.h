@@ -224,13 +224,17 @@ int qcd_sap_apply(qcd_ctx* ctx, void* out, const void* in, int n_sap, int n_jac,
 /* SAP domains independent of the context's storage blocking (Sec. 3; the
  * paper's runs use 16x6x4x3 to 16x12x8x12 domains, Tables 2-3).  sdom[4]:
  * extents of any size (not only powers of two) with every L_mu a multiple
- * of 2 sdom_mu and at most 1152 sites per domain; NULL returns to the
- * storage domains (the default).  With such domains every SAP application
- * (qcd_sap_apply, qcd_sap_apply_nrhs, qcd_solve) runs Algorithms 1-2 on them
- * with a kernel that holds one domain per CTA in shared memory (x and s in
- * float32) and reads links and C_inv from the internal layouts; sap_prec
- * must be QCD_PREC_SINGLE or QCD_PREC_HALF_GAUGE (QCD_ERR_ARG otherwise).
- * Errors: QCD_ERR_ARG for a domain that does not fit. */
+ * of 2 sdom_mu, and at most 1152 sites per domain or at most 8 time slices
+ * (sdom_t <= 8) of at most 448 sites (sdom_x sdom_y sdom_z <= 448); NULL
+ * returns to the storage domains (the default).  With such domains every
+ * SAP application (qcd_sap_apply, qcd_sap_apply_nrhs, qcd_solve) runs
+ * Algorithms 1-2 on them with a kernel that holds one domain per CTA in
+ * shared memory (x and s in float32, links and C_inv read from the internal
+ * layouts; domains up to 1152 sites) or, with float16 links and C_inv, one
+ * thread-block cluster per domain (see qcd_set_sap_shape); sap_prec must be
+ * QCD_PREC_SINGLE or QCD_PREC_HALF_GAUGE, and QCD_PREC_HALF_GAUGE with the
+ * cluster shape for domains above 1152 sites (QCD_ERR_ARG otherwise, at the
+ * SAP call).  Errors: QCD_ERR_ARG for a domain that fits neither kernel. */
 int qcd_set_sap_domain(qcd_ctx* ctx, const int sdom[4]);
 
 /* qcd_sap_apply for nrhs stacked fields (in and out hold nrhs internal

@@ -765,12 +765,15 @@ void sap_staged_sequence_h16g(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F
 void sap_apply_launch(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                       void* ws_s, void* ws_x16, void* ws_b16, cudaStream_t st);
 void workspace_reset_graphs(qcd_ctx* ctx);
-// SAP on the context's general domains (sap_dom, any extents up to 1152 sites)
+// SAP on the context's general domains (sap_dom, any extents; up to 1152
+// sites on the one-CTA kernel, larger ones on the cluster kernel)
 bool sap_domain_valid(const int dims[4], const int sdom[4]);
 void sap_general_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, int sap_prec,
                        void* ws_s, cudaStream_t st);
 // the same with one thread-block cluster per domain (float16 links and C_inv staged in shared memory)
 bool sap_cluster_eligible(const qcd_ctx* ctx, int sap_prec);
+bool sap_cluster_fits(const int sdom[4]);
+bool sap_general_fits(const int sdom[4]);  // the one-CTA kernel: at most 1152 sites
 void sap_cluster_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n_sap, int n_jac, void* ws_s,
                        cudaStream_t st);
 void gauge_import_launch(qcd_ctx* ctx, const double* u, cudaStream_t st);

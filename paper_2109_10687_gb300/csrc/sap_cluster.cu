@@ -384,11 +384,16 @@ __global__ void build_cluster_stage_kernel(Geom g, int sd0, int sd1, int sd2, in
     }
 }
 
+// a domain whose time slices fit the cluster kernel: at most CS_MAX_K
+// slices of at most CS_MAX_SLICE sites
+bool sap_cluster_fits(const int d[4]) {
+  const long long S = (long long)d[0] * d[1] * d[2];
+  return d[3] >= 1 && d[3] <= CS_MAX_K && S >= 1 && S <= CS_MAX_SLICE;
+}
+
 bool sap_cluster_eligible(const qcd_ctx* ctx, int sap_prec) {
   if (!ctx->sap_general || sap_prec != QCD_PREC_HALF_GAUGE) return false;
-  const int* d = ctx->sap_dom;
-  const int S = d[0] * d[1] * d[2];
-  return d[3] >= 1 && d[3] <= CS_MAX_K && S >= 1 && S <= CS_MAX_SLICE;
+  return sap_cluster_fits(ctx->sap_dom);
 }
 
 // build (or rebuild after a new clover term or domain) the staging copy

@@ -284,13 +284,16 @@ static void general_sequence(qcd_ctx* ctx, F32Spinor s_first_in, F32Spinor s, F3
   }
 }
 
+bool sap_general_fits(const int sdom[4]) {
+  return (long long)sdom[0] * sdom[1] * sdom[2] * sdom[3] <= GS_MAX_SITES;
+}
+
+// every extent divides the lattice into an even number of domains, and the
+// domain fits the one-CTA kernel or the cluster kernel
 bool sap_domain_valid(const int dims[4], const int sdom[4]) {
-  long long v = 1;
-  for (int mu = 0; mu < 4; ++mu) {
+  for (int mu = 0; mu < 4; ++mu)
     if (sdom[mu] < 1 || dims[mu] % (2 * sdom[mu])) return false;
-    v *= sdom[mu];
-  }
-  return v <= GS_MAX_SITES;
+  return sap_general_fits(sdom) || sap_cluster_fits(sdom);
 }
 
 // M_SAP for nrhs stacked float32 fields with the context's general SAP
@@ -306,6 +309,11 @@ void sap_general_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n
   QCD_REQUIRE(sap_prec == QCD_PREC_SINGLE || sap_prec == QCD_PREC_HALF_GAUGE, QCD_ERR_ARG,
               "SAP on general domains: sap_prec must be SINGLE or HALF_GAUGE");
   const bool can_cluster = sap_cluster_eligible(ctx, sap_prec);
+  const bool can_cta = sap_general_fits(ctx->sap_dom);
+  QCD_REQUIRE(can_cta || can_cluster, QCD_ERR_ARG,
+              "SAP on general domains: domains above 1152 sites run on the cluster kernel only (sap_prec HALF_GAUGE)");
+  QCD_REQUIRE(can_cta || ctx->sap_shape <= 0, QCD_ERR_ARG,
+              "SAP on general domains: domains above 1152 sites need the cluster shape (0 or autotuned)");
   const size_t v4 = (size_t)ctx->geom.vol * 6;
   auto run = [&](int v) {
     if (v == 0 && can_cluster) {
@@ -323,6 +331,7 @@ void sap_general_apply(qcd_ctx* ctx, float4* x, const float4* b, int nrhs, int n
     }
   };
   int v = ctx->sap_shape;
+  if (v < 0 && !can_cta) v = 0;
   if (v < 0) {
     if (can_cluster) {
       const Geom& g = ctx->geom;
@@ -350,7 +359,8 @@ extern "C" int qcd_set_sap_domain(qcd_ctx* ctx, const int sdom[4]) {
     return QCD_OK;
   }
   if (!sap_domain_valid(ctx->geom.L, sdom)) {
-    ctx->err = "qcd_set_sap_domain: every L_mu must be a multiple of 2 d_mu and a domain at most 1152 sites";
+    ctx->err = "qcd_set_sap_domain: every L_mu must be a multiple of 2 d_mu, and a domain at most 1152 sites or "
+               "at most 8 time slices of at most 448 sites";
     return QCD_ERR_ARG;
   }
   for (int mu = 0; mu < 4; ++mu) ctx->sap_dom[mu] = sdom[mu];
