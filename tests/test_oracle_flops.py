@@ -73,3 +73,16 @@ def test_dslash_roofline_constants():
     import bench
     assert bench.D_FLOP_PER_SITE == flops.D_FLOP_PER_SITE
     assert bench.D_BYTES_PER_SITE == 2 * 24 * 4 + 4 * 18 * 4 + 2 * 36 * 4 == 768
+
+
+def test_a64fx_node_rates_reproduce_table2_tflops():
+    """The A64FX node rates the benchmark compares against (site-iterations
+    per second of one node, from Table 2's times: four processes, each 500
+    iterations on a block of two domains) times the paper-basis flop per
+    site-iteration reproduce Table 2's TFLOPS column (0.8272 for 32x6x4x3,
+    1.0839 for 32x6x4x6) to its printed digits."""
+    import bench_configs
+    for domain, tflops in (((16, 6, 4, 3), 0.8272), ((16, 6, 4, 6), 1.0839)):
+        rate = bench_configs._a64fx_node_rate(domain)
+        flop = flops.flop_per_site_iter(domain, 4, 2)
+        assert abs(rate * flop / 1e12 - tflops) < 6e-5, (domain, rate * flop / 1e12)
