@@ -39,6 +39,18 @@ WORKLOAD = ("32^4 lattice, periodic space / antiperiodic time, chiral basis, U =
             "(4^4 domains, n_sap 4, n_jac 4) + float32 BiCGStab + float64 defect correction "
             "to true residual 1e-10")
 D_BYTES_PER_SITE = 96 + 96 + 4 * 72 + 288          # in + out spinor, 4 links (18 reals), clover
+D_BYTES_PER_SITE_12 = 96 + 96 + 4 * 48 + 288       # the same with links as their first two rows (12 reals)
+
+
+def d_bytes_per_site(tuning_lines, mode=0):
+    """Algorithmic bytes per site of the float32 D the autotuner chose: the
+    compressed-link variants (shape names ending in 'c') read 48 bytes per
+    link instead of 72."""
+    for ln in tuning_lines:
+        parts = ln.split()
+        if parts and parts[0].startswith(f"dslash_f32_mode{mode}_nrhs1") and len(parts) > 1:
+            return D_BYTES_PER_SITE_12 if parts[1].endswith("c") else D_BYTES_PER_SITE
+    return D_BYTES_PER_SITE
 D_FLOP_PER_SITE = 1824
 
 
@@ -566,7 +578,8 @@ def main():
     d_ms = e0.elapsed_time(e1) / nrep
     vol = int(np.prod(DIMS))
     peak, peak_kind = measured_peaks()
-    d_gbs = D_BYTES_PER_SITE * vol / (d_ms * 1e-3) / 1e9
+    d_bytes = d_bytes_per_site(B.qcd_tuning_report(lat.ctx).strip().splitlines())
+    d_gbs = d_bytes * vol / (d_ms * 1e-3) / 1e9
     d_gflops = D_FLOP_PER_SITE * vol / (d_ms * 1e-3) / 1e9
 
     # end to end through the public call with host buffers (pinned)
@@ -625,7 +638,7 @@ def main():
         "native_float64_residual": {"inner": info_df.inner_iters, "outer": info_df.outer_iters,
                                     "true_resid": info_df.true_resid},
         "dslash": {"kernel": "dslash_kernel<float, D>", "ms": d_ms, "gbs": d_gbs, "gflops": d_gflops,
-                   "bytes_per_site": D_BYTES_PER_SITE, "flop_per_site": D_FLOP_PER_SITE,
+                   "bytes_per_site": d_bytes, "flop_per_site": D_FLOP_PER_SITE,
                    "frac_of_hbm": d_gbs / peak, "peak_gbs": peak, "peak_kind": peak_kind},
         "roofline": {"kernel": "sap_staged_kernel<float16 storage>", "bound": "alu", "achieved": sap_tflops,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": sap_tflops / FP32_PEAK_TFLOPS,

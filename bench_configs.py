@@ -26,7 +26,7 @@ import time
 import numpy as np
 import torch
 
-from bench import D_BYTES_PER_SITE, D_FLOP_PER_SITE, ClockSampler, measured_peaks
+from bench import D_BYTES_PER_SITE, D_FLOP_PER_SITE, ClockSampler, d_bytes_per_site, measured_peaks
 
 
 def _smi_index():
@@ -82,9 +82,10 @@ def _dslash_gbs(lat, b_dev, nrep=20):
     ms = e0.elapsed_time(e1) / nrep
     vol = int(np.prod(lat.dims))
     peak, kind = measured_peaks()
-    gbs = D_BYTES_PER_SITE * vol / (ms * 1e-3) / 1e9
-    return {"ms": ms, "gbs": gbs, "gflops": D_FLOP_PER_SITE * vol / (ms * 1e-3) / 1e9, "frac_of_hbm": gbs / peak,
-            "peak_gbs": peak, "peak_kind": kind}
+    nbytes = d_bytes_per_site(B.qcd_tuning_report(lat.ctx).strip().splitlines())
+    gbs = nbytes * vol / (ms * 1e-3) / 1e9
+    return {"ms": ms, "gbs": gbs, "bytes_per_site": nbytes, "gflops": D_FLOP_PER_SITE * vol / (ms * 1e-3) / 1e9,
+            "frac_of_hbm": gbs / peak, "peak_gbs": peak, "peak_kind": kind}
 
 
 def c1(args):

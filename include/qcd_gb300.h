@@ -386,6 +386,17 @@ int qcd_profile_read(qcd_ctx* ctx, int kernel_class, long long* launches, double
  * then used). */
 int qcd_set_tuning(qcd_ctx* ctx, int enable);
 
+/* Links of the float32 D, D^dag and A (App. A) as 12 reals: an SU(3)
+ * matrix is fixed by its first two rows (the third is the complex conjugate
+ * of their cross product), so the HBM-bound operator can read 48 instead of
+ * 72 bytes per link and rebuild the third row.  mode -1 (default): the
+ * autotuner also times these variants when the links given to
+ * qcd_set_gauge are SU(3) to 1e-9; 0: never; 1: always (an operator call
+ * then returns QCD_ERR_STATE if the links are not SU(3) to 1e-9).  The
+ * rebuilt row differs from the stored float32 one by float32 rounding.
+ * QCD_ERR_ARG for other values. */
+int qcd_set_link_compression(qcd_ctx* ctx, int mode);
+
 /* Fix the SAP kernel's shape: -1 autotuned (default).  For 4^4 domains:
  * 0 one site per thread (256 threads per domain), 1 two sites per thread
  * (128 threads per domain, each thread two independent site streams), 2 one

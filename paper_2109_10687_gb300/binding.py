@@ -84,6 +84,7 @@ _SIGS = {
     "qcd_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "qcd_set_tuning": (_I, [_P, _I]),
     "qcd_set_sap_shape": (_I, [_P, _I]),
+    "qcd_set_link_compression": (_I, [_P, _I]),
     "qcd_set_sap_domain": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "qcd_tune_domain": (_I, [ctypes.POINTER(ctypes.c_int), _I, _I, _P, _P, _I, ctypes.c_double, ctypes.c_double,
                              ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int), _I,
@@ -293,6 +294,11 @@ def qcd_launch_count(ctx):
     n = ctypes.c_longlong()
     check(ctx, lib().qcd_launch_count(ctx, ctypes.byref(n)))
     return n.value
+
+
+def qcd_set_link_compression(ctx, mode):
+    """-1 autotuned (default), 0 never, 1 always: float32 D with 12-real links."""
+    return check(ctx, lib().qcd_set_link_compression(ctx, int(mode)))
 
 
 def qcd_set_tuning(ctx, enable=True):

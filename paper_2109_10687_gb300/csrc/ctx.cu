@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(CONV_THREADS) export_spinor_kernel(Geom g, dou
 // an optional SU(3) check that records the worst deviation in *bad (as the
 // bit pattern of a non-negative double, so integer atomicMax orders it).
 __global__ void gauge_import_kernel(Geom g, const double* __restrict__ src, double2* u64, float2* u32,
-                                    __half2* u16, unsigned long long* bad) {
+                                    __half2* u16, float4* u32c, unsigned long long* bad) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= g.vol) return;
   int x[4];
@@ -227,6 +227,12 @@ __global__ void gauge_import_kernel(Geom g, const double* __restrict__ src, doub
       u64[k] = make_double2(m[e / 3][e % 3].re, m[e / 3][e % 3].im);
       u32[k] = make_float2((float)m[e / 3][e % 3].re, (float)m[e / 3][e % 3].im);
       u16[k] = __floats2half2_rn((float)m[e / 3][e % 3].re, (float)m[e / 3][e % 3].im);
+    }
+    // the first two rows, three float4
+    const size_t cbase = ((size_t)((dom * 4 + mu) * 3)) << g.logvd;
+    for (int q = 0; q < 3; ++q) {
+      const cx<double> a = m[(2 * q) / 3][(2 * q) % 3], b = m[(2 * q + 1) / 3][(2 * q + 1) % 3];
+      u32c[cbase + ((size_t)q << g.logvd) + s] = make_float4((float)a.re, (float)a.im, (float)b.re, (float)b.im);
     }
     // |U^dag U - 1| and |det U - 1|
     for (int i = 0; i < 3; ++i)
@@ -383,7 +389,7 @@ extern "C" int qcd_destroy(qcd_ctx* ctx) {
   void* ptrs[] = {ctx->d_nbr, ctx->d_lex2dom, ctx->d_tflag, ctx->u64, ctx->u32, ctx->u16, ctx->clov64,
                   ctx->clov32, ctx->cinv64, ctx->cinv32, ctx->cinv16, ctx->d_status,
                   ctx->st_link16, ctx->st_link32, ctx->st_clov16, ctx->st_clov32, ctx->udf, ctx->clovdf,
-                  ctx->cl_link, ctx->cl_clov, ctx->flow_state};
+                  ctx->cl_link, ctx->cl_clov, ctx->flow_state, ctx->u32c};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
@@ -406,6 +412,7 @@ extern "C" int qcd_set_gauge(qcd_ctx* ctx, const double* U, int on_device, doubl
   ensure_alloc((void**)&ctx->u64, nlink * sizeof(double2));
   ensure_alloc((void**)&ctx->u32, nlink * sizeof(float2));
   ensure_alloc((void**)&ctx->u16, nlink * sizeof(__half2));
+  ensure_alloc((void**)&ctx->u32c, (size_t)g.vol * 4 * 3 * sizeof(float4));
   const double* src = U;
   double* tmp = nullptr;
   if (!on_device) {
@@ -417,7 +424,7 @@ extern "C" int qcd_set_gauge(qcd_ctx* ctx, const double* U, int on_device, doubl
   QCD_CUDA_CHECK(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st));
   {
     LaunchScope ls(ctx, QCD_KC_OTHER, st);
-    gauge_import_kernel<<<grid_for(g.vol, 128), 128, 0, st>>>(g, src, ctx->u64, ctx->u32, ctx->u16, bad);
+    gauge_import_kernel<<<grid_for(g.vol, 128), 128, 0, st>>>(g, src, ctx->u64, ctx->u32, ctx->u16, ctx->u32c, bad);
     check_launch();
   }
   unsigned long long hbad = 0;
@@ -428,6 +435,7 @@ extern "C" int qcd_set_gauge(qcd_ctx* ctx, const double* U, int on_device, doubl
   std::memcpy(&worst, &hbad, sizeof(worst));
   ctx->have_gauge = true;
   ctx->have_clover = false;
+  ctx->su3_links = worst <= 1e-9;
   if (check_tol > 0 && !(worst <= check_tol)) {
     ctx->have_gauge = false;
     char buf[160];

@@ -158,9 +158,9 @@ __device__ __forceinline__ void hopping(const Geom& g, const SIO& in, const LP& 
 // numbered rhs-fastest, so the nrhs blocks that share a tile of sites (and
 // its links and clover) run back to back and reuse them from L2.
 // One site (lexicographic-domain index gid) of one right-hand side.
-template <typename R, int MODE, bool HINT = false>
+template <typename R, int MODE, bool HINT = false, typename LP = typename Prec<R>::LP>
 __device__ __forceinline__ void dslash_site(const Geom& g, const typename Prec<R>::SIO& out,
-                                            const typename Prec<R>::SIO& in, const typename Prec<R>::LP& U,
+                                            const typename Prec<R>::SIO& in, const LP& U,
                                             const typename Prec<R>::CP& clov, R kappa, long long gid, int rhs) {
   // domains are visited in lexicographic order, so that the neighbouring
   // domains whose surface spinors a domain reads are processed at about the
@@ -195,17 +195,18 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const typename Prec<R
 // HINT: the clover rows and the output, touched once per application, are
 // read and written with the streaming (evict-first) cache operators, so
 // that L2 keeps the spinor and link lines that neighbouring sites read
-// again.  float32 only.
-template <typename R, int MODE, int THREADS, int MINB, bool HINT>
+// again.  float32 only.  LP: the links' storage (LinkPtr12: the first two
+// rows of SU(3) links, float32 only).
+template <typename R, int MODE, int THREADS, int MINB, bool HINT, typename LP = typename Prec<R>::LP>
 __global__ void __launch_bounds__(THREADS, MINB)
-    dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in, typename Prec<R>::LP U,
-                  typename Prec<R>::CP clov, R kappa, int nrhs) {
+    dslash_kernel(Geom g, typename Prec<R>::SIO out, typename Prec<R>::SIO in, LP U, typename Prec<R>::CP clov,
+                  R kappa, int nrhs) {
   const int rhs = blockIdx.x % nrhs;
   const long long gid = (blockIdx.x / nrhs) * (long long)THREADS + threadIdx.x;
   pdl_trigger();
   pdl_wait();
   if (gid >= g.vol || loop_idle(g)) return;
-  dslash_site<R, MODE, HINT>(g, out, in, U, clov, kappa, gid, rhs);
+  dslash_site<R, MODE, HINT, LP>(g, out, in, U, clov, kappa, gid, rhs);
 }
 
 // Ragged batch: one launch over several lattices of different sizes.  Block
@@ -322,26 +323,28 @@ __global__ void __launch_bounds__(128) ablock_kernel(Geom g, F32Spinor out, F32S
   out.store(g, dom, s, res);
 }
 
-template <typename R, int MODE, int THREADS, int MINB, bool HINT = false>
+template <typename R, int MODE, int THREADS, int MINB, bool HINT = false, typename LP = typename Prec<R>::LP>
 static void launch_dslash_shape(const Geom& g, void* out, const void* in, const void* U, const void* clov, R kappa,
                                 int nrhs, cudaStream_t st, bool pdl) {
   using P = Prec<R>;
   const long long blocks = (long long)grid_for(g.vol, THREADS) * nrhs;
   QCD_REQUIRE(blocks < (1LL << 31), QCD_ERR_ARG, "lattice too large for one launch");
   const typename P::SIO o{(decltype(P::SIO::p))out}, i{(decltype(P::SIO::p))in};
-  const typename P::LP u{(decltype(P::LP::p))U};
+  const LP u{(decltype(LP::p))U};
   const typename P::CP c{(decltype(P::CP::p))clov};
   if (pdl)
-    launch_pdl(dslash_kernel<R, MODE, THREADS, MINB, HINT>, dim3((unsigned)blocks), dim3(THREADS), 0, st, g, o, i, u, c,
-               kappa, nrhs);
+    launch_pdl(dslash_kernel<R, MODE, THREADS, MINB, HINT, LP>, dim3((unsigned)blocks), dim3(THREADS), 0, st, g, o, i, u,
+               c, kappa, nrhs);
   else
-    dslash_kernel<R, MODE, THREADS, MINB, HINT><<<(unsigned)blocks, THREADS, 0, st>>>(g, o, i, u, c, kappa, nrhs);
+    dslash_kernel<R, MODE, THREADS, MINB, HINT, LP><<<(unsigned)blocks, THREADS, 0, st>>>(g, o, i, u, c, kappa, nrhs);
 }
 
-// float32 launch shapes the autotuner chooses from
+// float32 launch shapes the autotuner chooses from: threads and blocks per
+// SM, streaming cache operators (h), and (c, variants 8-15, SU(3) links
+// only) the links read as their first two rows
 template <int MODE>
-static void launch_dslash_f32(int variant, const Geom& g, void* out, const void* in, const void* U, const void* clov,
-                              float kappa, int nrhs, cudaStream_t st, bool pdl) {
+static void launch_dslash_f32(int variant, const Geom& g, void* out, const void* in, const void* U, const void* U12,
+                              const void* clov, float kappa, int nrhs, cudaStream_t st, bool pdl) {
   switch (variant) {
     case 0: launch_dslash_shape<float, MODE, 128, 4>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
     case 1: launch_dslash_shape<float, MODE, 128, 5>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
@@ -350,7 +353,15 @@ static void launch_dslash_f32(int variant, const Geom& g, void* out, const void*
     case 4: launch_dslash_shape<float, MODE, 128, 4, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
     case 5: launch_dslash_shape<float, MODE, 128, 5, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
     case 6: launch_dslash_shape<float, MODE, 128, 6, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
-    default: launch_dslash_shape<float, MODE, 256, 2, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 7: launch_dslash_shape<float, MODE, 256, 2, true>(g, out, in, U, clov, kappa, nrhs, st, pdl); break;
+    case 8: launch_dslash_shape<float, MODE, 128, 4, false, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
+    case 9: launch_dslash_shape<float, MODE, 128, 5, false, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
+    case 10: launch_dslash_shape<float, MODE, 128, 6, false, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
+    case 11: launch_dslash_shape<float, MODE, 256, 2, false, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
+    case 12: launch_dslash_shape<float, MODE, 128, 4, true, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
+    case 13: launch_dslash_shape<float, MODE, 128, 5, true, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
+    case 14: launch_dslash_shape<float, MODE, 128, 6, true, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
+    default: launch_dslash_shape<float, MODE, 256, 2, true, LinkPtr12>(g, out, in, U12, clov, kappa, nrhs, st, pdl); break;
   }
 }
 // float64 launch shapes (register budget against resident warps)
@@ -367,8 +378,10 @@ static void launch_dslash_f64(int variant, const Geom& g, void* out, const void*
 static const char* kDslashShapes64[] = {"128x1", "128x2", "128x3", "128x4"};
 constexpr int kNumDslashShapes64 = 4;
 
-static const char* kDslashShapes[] = {"128x4", "128x5", "128x6", "256x2", "128x4h", "128x5h", "128x6h", "256x2h"};
-constexpr int kNumDslashShapes = 8;
+static const char* kDslashShapes[] = {"128x4",   "128x5",   "128x6",   "256x2",   "128x4h",   "128x5h",
+                                      "128x6h",  "256x2h",  "128x4c",  "128x5c",  "128x6c",   "256x2c",
+                                      "128x4hc", "128x5hc", "128x6hc", "256x2hc"};
+constexpr int kNumDslashShapes = 8;  // without the 8 compressed-link variants
 
 void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st,
                    bool pdl) {
@@ -399,14 +412,23 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
     const float k = (float)ctx->kappa;
     const void* clov = mode == MODE_A ? (const void*)ctx->cinv32 : (const void*)ctx->clov32;
     auto run = [&](int v) {
-      if (mode == MODE_A) launch_dslash_f32<MODE_A>(v, g, out, in, ctx->u32, clov, k, nrhs, st, pdl);
-      else if (mode == MODE_D) launch_dslash_f32<MODE_D>(v, g, out, in, ctx->u32, clov, k, nrhs, st, pdl);
-      else launch_dslash_f32<MODE_DDAG>(v, g, out, in, ctx->u32, clov, k, nrhs, st, pdl);
+      if (mode == MODE_A) launch_dslash_f32<MODE_A>(v, g, out, in, ctx->u32, ctx->u32c, clov, k, nrhs, st, pdl);
+      else if (mode == MODE_D) launch_dslash_f32<MODE_D>(v, g, out, in, ctx->u32, ctx->u32c, clov, k, nrhs, st, pdl);
+      else launch_dslash_f32<MODE_DDAG>(v, g, out, in, ctx->u32, ctx->u32c, clov, k, nrhs, st, pdl);
       check_launch();
     };
+    // the compressed-link variants only for links that are SU(3), all of
+    // them or none as qcd_set_link_compression asks (the key records which
+    // set the choice was made from)
+    QCD_REQUIRE(ctx->link12 != 1 || ctx->su3_links, QCD_ERR_STATE,
+                "float32 D with 12-real links: the links are not SU(3) to 1e-9");
+    const bool with12 = ctx->su3_links && ctx->link12 != 0;
+    const int base = ctx->link12 == 1 ? kNumDslashShapes : 0;
+    const int nv = ctx->link12 == 1 ? kNumDslashShapes : (with12 ? 2 * kNumDslashShapes : kNumDslashShapes);
     char key[64];
-    std::snprintf(key, sizeof key, "dslash_f32_mode%d_nrhs%d", mode, nrhs);
-    const int v = tune_pick(ctx, key, kNumDslashShapes, kDslashShapes, run, st);
+    std::snprintf(key, sizeof key, "dslash_f32_mode%d_nrhs%d%s", mode, nrhs,
+                  ctx->link12 == 1 ? "_links12" : (with12 ? "_su3" : ""));
+    const int v = base + tune_pick(ctx, key, nv, kDslashShapes + base, [&](int c) { run(base + c); }, st);
     LaunchScope ls(ctx, QCD_KC_DSLASH, st);
     run(v);
   } else {

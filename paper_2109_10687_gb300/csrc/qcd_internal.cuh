@@ -483,6 +483,35 @@ struct LinkPtr<double> {
     }
   }
 };
+// float32 links stored as their first two rows, 12 reals in three float4
+// per link ([dom][mu][3][vd]: (u00, u01), (u02, u10), (u11, u12)).  For an
+// SU(3) matrix the third row is the complex conjugate of the cross product
+// of the first two (unit determinant and unitarity), which the load rebuilds.
+struct LinkPtr12 {
+  const float4* p;
+  __device__ __forceinline__ void load(const Geom& g, int dom, int mu, int s, SU3<float>& u) const {
+    const size_t base = ((size_t)((dom * 4 + mu) * 3)) << g.logvd;
+    const float4 a = __ldg(p + base + s);
+    const float4 b = __ldg(p + base + ((size_t)1 << g.logvd) + s);
+    const float4 c = __ldg(p + base + ((size_t)2 << g.logvd) + s);
+    u.m[0][0] = make_cx(a.x, a.y);
+    u.m[0][1] = make_cx(a.z, a.w);
+    u.m[0][2] = make_cx(b.x, b.y);
+    u.m[1][0] = make_cx(b.z, b.w);
+    u.m[1][1] = make_cx(c.x, c.y);
+    u.m[1][2] = make_cx(c.z, c.w);
+    // conj(p q - r t) for the three cofactors
+    auto cof = [](cx<float> p, cx<float> q, cx<float> r, cx<float> t) {
+      const float re = fmaf(p.re, q.re, fmaf(-p.im, q.im, fmaf(-r.re, t.re, r.im * t.im)));
+      const float im = fmaf(p.re, q.im, fmaf(p.im, q.re, fmaf(-r.re, t.im, -r.im * t.re)));
+      return make_cx(re, -im);
+    };
+    u.m[2][0] = cof(u.m[0][1], u.m[1][2], u.m[0][2], u.m[1][1]);
+    u.m[2][1] = cof(u.m[0][2], u.m[1][0], u.m[0][0], u.m[1][2]);
+    u.m[2][2] = cof(u.m[0][0], u.m[1][1], u.m[0][1], u.m[1][0]);
+  }
+};
+
 struct LinkPtrHalf {
   const __half2* p;
   __device__ __forceinline__ void load(const Geom& g, int dom, int mu, int s, SU3<float>& u) const {
@@ -654,6 +683,9 @@ struct qcd_ctx {
   double2* u64 = nullptr;
   float2* u32 = nullptr;
   __half2* u16 = nullptr;
+  float4* u32c = nullptr;          // float32 links as their first two rows (12 reals, three float4)
+  bool su3_links = false;          // every link is SU(3) to 1e-9: the third row follows from the first two
+  int link12 = -1;                 // float32 D with links as 12 reals: -1 autotuned, 0 never, 1 always
   double2* clov64 = nullptr;     // 1 + C
   float4* clov32 = nullptr;
   double2* cinv64 = nullptr;     // (1 + C)^-1

@@ -156,6 +156,13 @@ extern "C" int qcd_tune_domain(const int dims[4], int bc_t, int basis, const dou
 
 extern "C" int qcd_tune_domain_default_count(void) { return (int)default_domains().size(); }
 
+extern "C" int qcd_set_link_compression(qcd_ctx* ctx, int mode) {
+  if (!ctx || mode < -1 || mode > 1) return QCD_ERR_ARG;
+  ctx->link12 = mode;
+  workspace_reset_graphs(ctx);
+  return QCD_OK;
+}
+
 extern "C" int qcd_set_sap_shape(qcd_ctx* ctx, int shape) {
   if (!ctx || shape < -1 || shape > 4) return QCD_ERR_ARG;
   ctx->sap_shape = shape;

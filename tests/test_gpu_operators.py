@@ -56,6 +56,24 @@ def test_A(prob):
     assert rel_l2(to_np(prob.lat.apply_A(x)), prob.op.A(x)) <= 1e-6
 
 
+@pytest.mark.parametrize("mode", [1, 0])
+def test_float32_operators_with_12_real_links(prob, mode):
+    """The float32 D, D^dag and A with the links read as their first two
+    rows and the third rebuilt as the conjugated cross product (forced on,
+    mode 1), and never (mode 0): both within 1e-6 of the oracle."""
+    from paper_2109_10687_gb300 import binding as B
+    x = prob.source(2008)
+    try:
+        B.qcd_set_link_compression(prob.lat.ctx, mode)
+        assert rel_l2(to_np(prob.lat.apply_D(x, "single")), prob.op.D(x)) <= 1e-6
+        assert rel_l2(to_np(prob.lat.apply_D(x, "single", dagger=True)), prob.op.Ddag(x)) <= 1e-6
+        assert rel_l2(to_np(prob.lat.apply_A(x)), prob.op.A(x)) <= 1e-6
+        if mode == 1:
+            assert "_links12" in B.qcd_tuning_report(prob.lat.ctx)
+    finally:
+        B.qcd_set_link_compression(prob.lat.ctx, -1)
+
+
 @pytest.mark.parametrize("prec,tol", [("single", 1e-6), ("double", 1e-13)])
 def test_clover_and_inverse(prob, prec, tol):
     x = prob.source(2004)
@@ -121,6 +139,32 @@ def test_set_gauge_rejects_non_su3():
         with pytest.raises(B.QcdError) as e:
             p.lat.set_gauge(bad, check_tol=1e-10)
         assert e.value.code == B.QCD_ERR_ARG
+    finally:
+        p.close()
+
+
+def test_12_real_links_need_su3_links():
+    """Links that are unitary but not special (a U(1) phase on every link,
+    set without the SU(3) check) cannot be rebuilt from two rows: forcing
+    the 12-real variants makes the operator call return QCD_ERR_STATE, the
+    autotuned default does not offer them, and the result stays correct."""
+    from paper_2109_10687_gb300 import binding as B
+    from oracle.dirac import CloverWilson
+    p = Problem((8, 8, 8, 8), (4, 4, 4, 4), seed=1005, oracle=False)
+    try:
+        u = p.u * np.exp(0.3j)
+        p.lat.set_gauge(u, check_tol=0)
+        B.qcd_build_clover(p.lat.ctx)
+        x = p.source(2009)
+        a = p.lat.to_internal(x, "single")
+        o = p.lat.field("single")
+        B.qcd_set_link_compression(p.lat.ctx, 1)
+        assert B.lib().qcd_apply_D(p.lat.ctx, B._ptr(o), B._ptr(a), B.PREC_SINGLE, 0, 1, None) == B.QCD_ERR_STATE
+        B.qcd_set_link_compression(p.lat.ctx, -1)
+        op = CloverWilson(u, p.kappa, p.csw, p.gammas, bc_t=-1)
+        assert rel_l2(to_np(p.lat.apply_D(x, "single")), op.D(x)) <= 1e-6
+        assert "_su3" not in B.qcd_tuning_report(p.lat.ctx)
+        assert B.lib().qcd_set_link_compression(p.lat.ctx, 2) == B.QCD_ERR_ARG
     finally:
         p.close()
 

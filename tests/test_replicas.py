@@ -109,3 +109,19 @@ def test_cpu_config_oracle_jobs():
     wall, (t_d, t_it) = bench_configs._oracle_pool([("D", (8, 8, 8, 8)), ("iter", (8, 8, 8, 8))], 1)
     assert 0 < t_d < t_it <= wall
     assert os.environ.get("OMP_NUM_THREADS") == before
+
+
+def test_d_bytes_follow_the_tuned_link_format():
+    """The benchmark counts the float32 D's algorithmic bytes for the link
+    format the autotuner chose: 768 B per site with 18-real links, 672 with
+    the 12-real variants (shape names ending in 'c')."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.D_BYTES_PER_SITE == 768 and bench.D_BYTES_PER_SITE_12 == 672
+    full = ["dslash_f32_mode0_nrhs1_su3 128x4h 0.1400 ms [128x4 0.1437, 128x4c 0.1450]"]
+    comp = ["dslash_f32_mode0_nrhs1_su3 128x4hc 0.1250 ms [128x4 0.1437, 128x4hc 0.1250]"]
+    other = ["dslash_f32_mode2_nrhs1_su3 128x4hc 0.1250 ms [128x4hc 0.1250]"]
+    assert bench.d_bytes_per_site(full) == 768
+    assert bench.d_bytes_per_site(comp) == 672
+    assert bench.d_bytes_per_site(other) == 768  # mode 2 (A) is not the D
+    assert bench.d_bytes_per_site(other, mode=2) == 672
