@@ -43,12 +43,13 @@ D_BYTES_PER_SITE_12 = 96 + 96 + 4 * 48 + 288       # the same with links as thei
 
 
 def d_bytes_per_site(tuning_lines, mode=0):
-    """Algorithmic bytes per site of the float32 D the autotuner chose: the
-    compressed-link variants (shape names ending in 'c') read 48 bytes per
-    link instead of 72."""
+    """Algorithmic bytes per site of the float32 D that ran (the last tuned
+    shape for the operator): the 12-real-link variants (shape names ending
+    in 'c') read 48 bytes per link instead of 72."""
+    key = f"dslash_f32_mode{mode}_nrhs1"
     for ln in tuning_lines:
         parts = ln.split()
-        if parts and parts[0].startswith(f"dslash_f32_mode{mode}_nrhs1") and len(parts) > 1:
+        if len(parts) > 1 and (parts[0] == key or parts[0].startswith(key + "_")):
             return D_BYTES_PER_SITE_12 if parts[1].endswith("c") else D_BYTES_PER_SITE
     return D_BYTES_PER_SITE
 D_FLOP_PER_SITE = 1824

@@ -389,11 +389,12 @@ int qcd_set_tuning(qcd_ctx* ctx, int enable);
 /* Links of the float32 D, D^dag and A (App. A) as 12 reals: an SU(3)
  * matrix is fixed by its first two rows (the third is the complex conjugate
  * of their cross product), so the HBM-bound operator can read 48 instead of
- * 72 bytes per link and rebuild the third row.  mode -1 (default): the
- * autotuner also times these variants when the links given to
- * qcd_set_gauge are SU(3) to 1e-9; 0: never; 1: always (an operator call
- * then returns QCD_ERR_STATE if the links are not SU(3) to 1e-9).  The
- * rebuilt row differs from the stored float32 one by float32 rounding.
+ * 72 bytes per link and rebuild the third row.  mode -1 (default): 12
+ * reals whenever the links given to qcd_set_gauge are SU(3) to 1e-9; 0:
+ * never; 1: always (an operator call then returns QCD_ERR_STATE if the
+ * links are not SU(3) to 1e-9).  The format is fixed by this setting and
+ * the links, not by the autotuner, whose launch shapes stay bit-identical;
+ * the rebuilt row differs from the stored float32 one by float32 rounding.
  * QCD_ERR_ARG for other values. */
 int qcd_set_link_compression(qcd_ctx* ctx, int mode);
 

@@ -340,8 +340,8 @@ static void launch_dslash_shape(const Geom& g, void* out, const void* in, const 
 }
 
 // float32 launch shapes the autotuner chooses from: threads and blocks per
-// SM, streaming cache operators (h), and (c, variants 8-15, SU(3) links
-// only) the links read as their first two rows
+// SM and streaming cache operators (h); variants 8-15 (c) are the same
+// shapes with the links read as their first two rows (SU(3) links)
 template <int MODE>
 static void launch_dslash_f32(int variant, const Geom& g, void* out, const void* in, const void* U, const void* U12,
                               const void* clov, float kappa, int nrhs, cudaStream_t st, bool pdl) {
@@ -381,7 +381,7 @@ constexpr int kNumDslashShapes64 = 4;
 static const char* kDslashShapes[] = {"128x4",   "128x5",   "128x6",   "256x2",   "128x4h",   "128x5h",
                                       "128x6h",  "256x2h",  "128x4c",  "128x5c",  "128x6c",   "256x2c",
                                       "128x4hc", "128x5hc", "128x6hc", "256x2hc"};
-constexpr int kNumDslashShapes = 8;  // without the 8 compressed-link variants
+constexpr int kNumDslashShapes = 8;  // shapes per link format
 
 void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, int nrhs, cudaStream_t st,
                    bool pdl) {
@@ -417,18 +417,18 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
       else launch_dslash_f32<MODE_DDAG>(v, g, out, in, ctx->u32, ctx->u32c, clov, k, nrhs, st, pdl);
       check_launch();
     };
-    // the compressed-link variants only for links that are SU(3), all of
-    // them or none as qcd_set_link_compression asks (the key records which
-    // set the choice was made from)
+    // The link format is not the tuner's to choose, since it changes the
+    // arithmetic (the rebuilt row differs from the stored one by float32
+    // rounding) and the tuner's choices may change scheduling only: 12-real
+    // links whenever the links are SU(3), unless qcd_set_link_compression
+    // says otherwise; the tuner picks among that format's launch shapes.
     QCD_REQUIRE(ctx->link12 != 1 || ctx->su3_links, QCD_ERR_STATE,
                 "float32 D with 12-real links: the links are not SU(3) to 1e-9");
-    const bool with12 = ctx->su3_links && ctx->link12 != 0;
-    const int base = ctx->link12 == 1 ? kNumDslashShapes : 0;
-    const int nv = ctx->link12 == 1 ? kNumDslashShapes : (with12 ? 2 * kNumDslashShapes : kNumDslashShapes);
+    const bool use12 = ctx->link12 == 1 || (ctx->link12 == -1 && ctx->su3_links);
+    const int base = use12 ? kNumDslashShapes : 0;
     char key[64];
-    std::snprintf(key, sizeof key, "dslash_f32_mode%d_nrhs%d%s", mode, nrhs,
-                  ctx->link12 == 1 ? "_links12" : (with12 ? "_su3" : ""));
-    const int v = base + tune_pick(ctx, key, nv, kDslashShapes + base, [&](int c) { run(base + c); }, st);
+    std::snprintf(key, sizeof key, "dslash_f32_mode%d_nrhs%d%s", mode, nrhs, use12 ? "_links12" : "");
+    const int v = base + tune_pick(ctx, key, kNumDslashShapes, kDslashShapes + base, [&](int c) { run(base + c); }, st);
     LaunchScope ls(ctx, QCD_KC_DSLASH, st);
     run(v);
   } else {

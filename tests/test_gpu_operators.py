@@ -59,8 +59,9 @@ def test_A(prob):
 @pytest.mark.parametrize("mode", [1, 0])
 def test_float32_operators_with_12_real_links(prob, mode):
     """The float32 D, D^dag and A with the links read as their first two
-    rows and the third rebuilt as the conjugated cross product (forced on,
-    mode 1), and never (mode 0): both within 1e-6 of the oracle."""
+    rows and the third rebuilt as the conjugated cross product (mode 1, and
+    the default for these SU(3) links), and never (mode 0): both within
+    1e-6 of the oracle."""
     from paper_2109_10687_gb300 import binding as B
     x = prob.source(2008)
     try:
@@ -147,7 +148,7 @@ def test_12_real_links_need_su3_links():
     """Links that are unitary but not special (a U(1) phase on every link,
     set without the SU(3) check) cannot be rebuilt from two rows: forcing
     the 12-real variants makes the operator call return QCD_ERR_STATE, the
-    autotuned default does not offer them, and the result stays correct."""
+    default does not use them, and the result stays correct."""
     from paper_2109_10687_gb300 import binding as B
     from oracle.dirac import CloverWilson
     p = Problem((8, 8, 8, 8), (4, 4, 4, 4), seed=1005, oracle=False)
@@ -163,7 +164,7 @@ def test_12_real_links_need_su3_links():
         B.qcd_set_link_compression(p.lat.ctx, -1)
         op = CloverWilson(u, p.kappa, p.csw, p.gammas, bc_t=-1)
         assert rel_l2(to_np(p.lat.apply_D(x, "single")), op.D(x)) <= 1e-6
-        assert "_su3" not in B.qcd_tuning_report(p.lat.ctx)
+        assert "_links12" not in B.qcd_tuning_report(p.lat.ctx)
         assert B.lib().qcd_set_link_compression(p.lat.ctx, 2) == B.QCD_ERR_ARG
     finally:
         p.close()

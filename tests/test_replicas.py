@@ -118,10 +118,12 @@ def test_d_bytes_follow_the_tuned_link_format():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.D_BYTES_PER_SITE == 768 and bench.D_BYTES_PER_SITE_12 == 672
-    full = ["dslash_f32_mode0_nrhs1_su3 128x4h 0.1400 ms [128x4 0.1437, 128x4c 0.1450]"]
-    comp = ["dslash_f32_mode0_nrhs1_su3 128x4hc 0.1250 ms [128x4 0.1437, 128x4hc 0.1250]"]
-    other = ["dslash_f32_mode2_nrhs1_su3 128x4hc 0.1250 ms [128x4hc 0.1250]"]
+    full = ["dslash_f32_mode0_nrhs1 128x4h 0.1400 ms [128x4 0.1437, 128x4h 0.1400]"]
+    comp = ["dslash_f32_mode0_nrhs1_links12 128x4hc 0.1210 ms [128x4c 0.1233, 128x4hc 0.1210]"]
+    other = ["dslash_f32_mode2_nrhs1_links12 128x4hc 0.1240 ms [128x4hc 0.1240]"]
+    many = ["dslash_f32_mode0_nrhs12_links12 128x4hc 1.4 ms [128x4hc 1.4]"] + full
     assert bench.d_bytes_per_site(full) == 768
     assert bench.d_bytes_per_site(comp) == 672
     assert bench.d_bytes_per_site(other) == 768  # mode 2 (A) is not the D
     assert bench.d_bytes_per_site(other, mode=2) == 672
+    assert bench.d_bytes_per_site(many) == 768  # the 12-rhs key is not the single-rhs one
