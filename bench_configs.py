@@ -291,7 +291,10 @@ def ragged_batch(reps=3, precs=("half", "half_gauge"), dslash=True):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / nrep
         peak, kind = measured_peaks()
-        gbs = D_BYTES_PER_SITE * sum(vols) / (ms * 1e-3) / 1e9
+        # bytes of the link format the lattices' operators use (12 or 18 reals)
+        nbytes = sum((D_BYTES_PER_SITE - 4 * 24 if B.qcd_link_format(l.ctx) == 12 else D_BYTES_PER_SITE) * v
+                     for l, v in zip(lats, vols))
+        gbs = nbytes / (ms * 1e-3) / 1e9
         res["dslash_batched"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak, "peak_kind": kind}
     xs = [torch.zeros_like(b) for b in bs]
     solves = {}

@@ -398,6 +398,11 @@ int qcd_set_tuning(qcd_ctx* ctx, int enable);
  * QCD_ERR_ARG for other values. */
 int qcd_set_link_compression(qcd_ctx* ctx, int mode);
 
+/* *reals = 12 or 18: the link format the float32 operators (single and
+ * batched) use now, as qcd_set_link_compression and the links decide.
+ * QCD_ERR_ARG for null arguments. */
+int qcd_link_format(const qcd_ctx* ctx, int* reals);
+
 /* Fix the SAP kernel's shape: -1 autotuned (default).  For 4^4 domains:
  * 0 one site per thread (256 threads per domain), 1 two sites per thread
  * (128 threads per domain, each thread two independent site streams), 2 one

@@ -85,6 +85,7 @@ _SIGS = {
     "qcd_set_tuning": (_I, [_P, _I]),
     "qcd_set_sap_shape": (_I, [_P, _I]),
     "qcd_set_link_compression": (_I, [_P, _I]),
+    "qcd_link_format": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "qcd_set_sap_domain": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "qcd_tune_domain": (_I, [ctypes.POINTER(ctypes.c_int), _I, _I, _P, _P, _I, ctypes.c_double, ctypes.c_double,
                              ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int), _I,
@@ -299,6 +300,13 @@ def qcd_launch_count(ctx):
 def qcd_set_link_compression(ctx, mode):
     """-1 autotuned (default), 0 never, 1 always: float32 D with 12-real links."""
     return check(ctx, lib().qcd_set_link_compression(ctx, int(mode)))
+
+
+def qcd_link_format(ctx):
+    """12 or 18: the link format the float32 operators use now."""
+    r = ctypes.c_int()
+    check(ctx, lib().qcd_link_format(ctx, ctypes.byref(r)))
+    return r.value
 
 
 def qcd_set_tuning(ctx, enable=True):

@@ -97,6 +97,9 @@ extern "C" int qcd_batch_apply_D(qcd_batch* b, void* const* out, const void* con
       d.out = (float4*)out[i];
       d.in = (const float4*)in[i];
       d.u = c->u32;
+      QCD_REQUIRE(c->link12 != 1 || c->su3_links, QCD_ERR_STATE,
+                  "batched D with 12-real links: a lattice's links are not SU(3) to 1e-9");
+      d.u12 = uses_links12(c) ? c->u32c : nullptr;
       d.clov = c->clov32;
       d.kappa = (float)c->kappa;
       d.block_begin = blocks;

@@ -227,10 +227,16 @@ __global__ void __launch_bounds__(128, 4) dslash_batch_kernel(const BatchDesc* _
   const long long gid = ((long long)blockIdx.x - sd.block_begin) * 128 + threadIdx.x;
   if (gid >= sd.g.vol) return;
   const F32Spinor out{sd.out}, in{(float4*)sd.in};
-  const LinkPtr<float> U{sd.u};
   const CloverPtrF32 clov{sd.clov};
-  if (dagger) dslash_site<float, MODE_DDAG, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
-  else dslash_site<float, MODE_D, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
+  if (sd.u12) {  // this lattice's links as 12 reals (uniform over the block)
+    const LinkPtr12 U{sd.u12};
+    if (dagger) dslash_site<float, MODE_DDAG, true, LinkPtr12>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
+    else dslash_site<float, MODE_D, true, LinkPtr12>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
+  } else {
+    const LinkPtr<float> U{sd.u};
+    if (dagger) dslash_site<float, MODE_DDAG, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
+    else dslash_site<float, MODE_D, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
+  }
 }
 
 void dslash_batch_launch(const BatchDesc* d_desc, const int* d_block_lat, long long total_blocks, int dagger,
@@ -258,10 +264,13 @@ __global__ void __launch_bounds__(128, 3) lat_dslash_a_kernel(const LatDesc* __r
   if (loop_idle(sd.g) || *(volatile const int*)sd.done) return;
   const long long gid = ((long long)blockIdx.x - sd.block_begin) * 128 + threadIdx.x;
   if (gid >= sd.g.vol) return;
-  const LinkPtr<float> U{sd.u32};
   const CloverPtrF32 cinv{sd.cinv32};
-  if (which == 0) dslash_site<float, MODE_A, true>(sd.g, F32Spinor{sd.q}, F32Spinor{sd.zp}, U, cinv, sd.kappa, gid, 0);
-  else dslash_site<float, MODE_A, true>(sd.g, F32Spinor{sd.t}, F32Spinor{sd.zr}, U, cinv, sd.kappa, gid, 0);
+  const F32Spinor o{which == 0 ? sd.q : sd.t}, i{which == 0 ? sd.zp : sd.zr};
+  if (sd.u32c) {  // this lattice's links as 12 reals (uniform over the block)
+    dslash_site<float, MODE_A, true, LinkPtr12>(sd.g, o, i, LinkPtr12{sd.u32c}, cinv, sd.kappa, gid, 0);
+  } else {
+    dslash_site<float, MODE_A, true>(sd.g, o, i, LinkPtr<float>{sd.u32}, cinv, sd.kappa, gid, 0);
+  }
 }
 __global__ void __launch_bounds__(128) lat_dslash64_kernel(const LatDesc* __restrict__ desc,
                                                            const int* __restrict__ block_lat) {
@@ -424,7 +433,7 @@ void dslash_launch(qcd_ctx* ctx, void* out, const void* in, int prec, int mode, 
     // says otherwise; the tuner picks among that format's launch shapes.
     QCD_REQUIRE(ctx->link12 != 1 || ctx->su3_links, QCD_ERR_STATE,
                 "float32 D with 12-real links: the links are not SU(3) to 1e-9");
-    const bool use12 = ctx->link12 == 1 || (ctx->link12 == -1 && ctx->su3_links);
+    const bool use12 = uses_links12(ctx);
     const int base = use12 ? kNumDslashShapes : 0;
     char key[64];
     std::snprintf(key, sizeof key, "dslash_f32_mode%d_nrhs%d%s", mode, nrhs, use12 ? "_links12" : "");

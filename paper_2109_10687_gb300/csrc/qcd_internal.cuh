@@ -685,7 +685,7 @@ struct qcd_ctx {
   __half2* u16 = nullptr;
   float4* u32c = nullptr;          // float32 links as their first two rows (12 reals, three float4)
   bool su3_links = false;          // every link is SU(3) to 1e-9: the third row follows from the first two
-  int link12 = -1;                 // float32 D with links as 12 reals: -1 autotuned, 0 never, 1 always
+  int link12 = -1;                 // float32 D with links as 12 reals: -1 when SU(3), 0 never, 1 always
   double2* clov64 = nullptr;     // 1 + C
   float4* clov32 = nullptr;
   double2* cinv64 = nullptr;     // (1 + C)^-1
@@ -717,6 +717,15 @@ struct qcd_ctx {
   long long launches = 0;
   std::string err;
 };
+
+namespace qcd {
+// whether a context's float32 operator reads its links as 12 reals (its
+// links are SU(3) and qcd_set_link_compression does not forbid it, or asks
+// for it)
+inline bool uses_links12(const qcd_ctx* ctx) {
+  return ctx->link12 == 1 || (ctx->link12 == -1 && ctx->su3_links);
+}
+}  // namespace qcd
 
 namespace qcd {
 
@@ -822,6 +831,7 @@ struct BatchDesc {
   float4* out;
   const float4* in;
   const float2* u;
+  const float4* u12;      // the links as 12 reals, when this lattice's operator uses them (else null)
   const float4* clov;
   float kappa;
   long long block_begin;  // first block of this lattice in the batched launch
@@ -837,6 +847,7 @@ struct LatDesc {
   float kappa;
   double kappa64;
   const float2* u32;
+  const float4* u32c;                  // the links as 12 reals, or null (as uses_links12)
   const float4* cinv32;
   const double2* u64;
   const double2* clov64;

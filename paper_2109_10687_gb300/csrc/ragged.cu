@@ -62,6 +62,7 @@ struct RaggedWS {
   long long nloop = 0;
   cudaStream_t st = nullptr;
   std::vector<int> clover_gen;  // each lattice's clover build the descriptors were made from
+  std::vector<bool> links12;    // and each lattice's float32 link format
 };
 
 void ragged_free(RaggedWS* w) {
@@ -199,9 +200,11 @@ __global__ void __launch_bounds__(128) k_rg_axpy(const LatDesc* __restrict__ des
 static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
   if (wp) {
     // descriptors and SAP plans hold kappa and pointers taken at the first
-    // solve: rebuild them after any lattice's clover term was rebuilt
+    // solve: rebuild them after any lattice's clover term was rebuilt or its
+    // link format changed
     bool same = true;
-    for (size_t i = 0; i < ctx.size(); ++i) same = same && wp->clover_gen[i] == ctx[i]->clover_gen;
+    for (size_t i = 0; i < ctx.size(); ++i)
+      same = same && wp->clover_gen[i] == ctx[i]->clover_gen && wp->links12[i] == uses_links12(ctx[i]);
     if (same) return wp;
     QCD_CUDA_CHECK(cudaDeviceSynchronize());
     ragged_free(wp);
@@ -269,6 +272,9 @@ static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
       d.kappa = (float)c->kappa;
       d.kappa64 = c->kappa;
       d.u32 = c->u32;
+      QCD_REQUIRE(c->link12 != 1 || c->su3_links, QCD_ERR_STATE,
+                  "batch solve with 12-real links: a lattice's links are not SU(3) to 1e-9");
+      d.u32c = uses_links12(c) ? c->u32c : nullptr;
       d.cinv32 = c->cinv32;
       d.u64 = c->u64;
       d.clov64 = c->clov64;
@@ -293,7 +299,10 @@ static RaggedWS* ragged_ws(const std::vector<qcd_ctx*>& ctx, RaggedWS*& wp) {
     QCD_CUDA_CHECK(cudaMalloc(&w->d_tile_lat, sizeof(int) * tile_lat.size()));
     QCD_CUDA_CHECK(cudaMemcpy(w->d_tile_lat, tile_lat.data(), sizeof(int) * tile_lat.size(), cudaMemcpyHostToDevice));
     QCD_CUDA_CHECK(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
-    for (const qcd_ctx* c : ctx) w->clover_gen.push_back(c->clover_gen);
+    for (const qcd_ctx* c : ctx) {
+      w->clover_gen.push_back(c->clover_gen);
+      w->links12.push_back(uses_links12(c));
+    }
   } catch (...) {
     ragged_free(w);
     throw;

@@ -163,6 +163,12 @@ extern "C" int qcd_set_link_compression(qcd_ctx* ctx, int mode) {
   return QCD_OK;
 }
 
+extern "C" int qcd_link_format(const qcd_ctx* ctx, int* reals) {
+  if (!ctx || !reals) return QCD_ERR_ARG;
+  *reals = uses_links12(ctx) ? 12 : 18;
+  return QCD_OK;
+}
+
 extern "C" int qcd_set_sap_shape(qcd_ctx* ctx, int shape) {
   if (!ctx || shape < -1 || shape > 4) return QCD_ERR_ARG;
   ctx->sap_shape = shape;

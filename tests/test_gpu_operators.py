@@ -65,7 +65,9 @@ def test_float32_operators_with_12_real_links(prob, mode):
     from paper_2109_10687_gb300 import binding as B
     x = prob.source(2008)
     try:
+        assert B.qcd_link_format(prob.lat.ctx) == 12  # the default for SU(3) links
         B.qcd_set_link_compression(prob.lat.ctx, mode)
+        assert B.qcd_link_format(prob.lat.ctx) == (12 if mode == 1 else 18)
         assert rel_l2(to_np(prob.lat.apply_D(x, "single")), prob.op.D(x)) <= 1e-6
         assert rel_l2(to_np(prob.lat.apply_D(x, "single", dagger=True)), prob.op.Ddag(x)) <= 1e-6
         assert rel_l2(to_np(prob.lat.apply_A(x)), prob.op.A(x)) <= 1e-6
@@ -162,6 +164,7 @@ def test_12_real_links_need_su3_links():
         B.qcd_set_link_compression(p.lat.ctx, 1)
         assert B.lib().qcd_apply_D(p.lat.ctx, B._ptr(o), B._ptr(a), B.PREC_SINGLE, 0, 1, None) == B.QCD_ERR_STATE
         B.qcd_set_link_compression(p.lat.ctx, -1)
+        assert B.qcd_link_format(p.lat.ctx) == 18
         op = CloverWilson(u, p.kappa, p.csw, p.gammas, bc_t=-1)
         assert rel_l2(to_np(p.lat.apply_D(x, "single")), op.D(x)) <= 1e-6
         assert "_links12" not in B.qcd_tuning_report(p.lat.ctx)
