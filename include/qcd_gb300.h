@@ -263,7 +263,7 @@ int qcd_norm2(qcd_ctx* ctx, double* result, const void* a, int prec, int nrhs, v
  * held by every GPU that loads the library until the process exits.  Limits:
  * 1 <= nrhs <= 16 (QCD_ERR_ARG otherwise).  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every
+ * device current.  Every
  * call shares the one array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * result: host pointer, nrhs doubles; a: internal-layout field of precision
