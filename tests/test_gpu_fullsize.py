@@ -233,3 +233,42 @@ def test_one_launch_msap_at_32x4_equals_per_launch(sap_prec):
     finally:
         B.qcd_set_sap_shape(lat.ctx, -1)
         lat.close()
+
+
+def test_msap_32x4_twelve_rhs():
+    """The benchmark's 32^4 lattice (4096 domains) with 12 right-hand sides
+    through every SAP launch, float16 links and C_inv with float32 vectors:
+    right-hand sides 0, 5 and 11 equal their single-rhs M_SAP bit for bit;
+    M_SAP is linear to float32 rounding (M(b_0 + 2 b_1) against
+    M b_0 + 2 M b_1); and A M_SAP stays close to the identity
+    (|b - A M_SAP b| / |b| < 0.5), a property of the Schwarz preconditioner
+    at any size."""
+    from paper_2109_10687_gb300 import binding as B
+    from paper_2109_10687_gb300.lattice import Lattice
+    dims = (32, 32, 32, 32)
+    lat = Lattice(dims, (4, 4, 4, 4), -1, "chiral").setup(random_su3_field_fast(dims, 0.3, 1001), 0.125, 1.0)
+    try:
+        b = torch.view_as_real(torch.from_numpy(gaussian_spinor(dims, 2201))).cuda()
+        srcs = torch.stack([(1.0 + r / 12) * b.roll(r, r % 4) for r in range(12)]).contiguous()
+        nb = B.qcd_field_bytes(lat.ctx, B.PREC_SINGLE, 1)
+        a = lat.field("single", 12)
+        B.qcd_import_spinor(lat.ctx, a, srcs, B.PREC_SINGLE, 12)
+        o = lat.field("single", 12)
+        B.qcd_sap_apply_nrhs(lat.ctx, o, a, 12, 4, 4, B.PREC_HALF_GAUGE, 0)
+        one = lat.field("single", 1)
+        for r in (0, 5, 11):
+            B.qcd_sap_apply_nrhs(lat.ctx, one, a[r * nb:(r + 1) * nb], 1, 4, 4, B.PREC_HALF_GAUGE, 0)
+            assert torch.equal(one, o[r * nb:(r + 1) * nb]), r
+        m0 = lat.to_canonical(o[0:nb])
+        m1 = lat.to_canonical(o[nb:2 * nb])
+        comb = lat.to_internal(torch.view_as_complex(srcs[0] + 2.0 * srcs[1]))
+        B.qcd_sap_apply_nrhs(lat.ctx, one, comb, 1, 4, 4, B.PREC_HALF_GAUGE, 0)
+        lin = lat.to_canonical(one)
+        assert rel_l2(to_np(lin), to_np(m0 + 2.0 * m1)) <= 1e-5
+        B.qcd_sap_apply_nrhs(lat.ctx, o, a, 12, 4, 4, B.PREC_HALF_GAUGE, 1)
+        for r in (0, 11):
+            amb = to_np(lat.to_canonical(o[r * nb:(r + 1) * nb]))
+            assert rel_l2(amb, to_np(torch.view_as_complex(srcs[r]))) < 0.5, r
+        assert B.qcd_device_status(lat.ctx) == B.QCD_OK
+    finally:
+        lat.close()
