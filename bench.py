@@ -668,7 +668,7 @@ def main():
         # plain float32 solves (outside the headline's timed region)
         import bench_configs
         barrier()
-        line["north_star_48x4"] = bench_configs.north_star_48x4(reps=1)
+        line["batched_48x4_12_point_sources"] = bench_configs.batched_48x4_12_point_sources(reps=1)
         barrier()
     if not args.no_n2:
         # the paper's parameters (n_sap 4, n_jac 2) on its own 16x6x4x3 SAP

@@ -124,7 +124,7 @@ def per_rhs_resid(lat, x, b, nrhs):
     return out
 
 
-def north_star_48x4(reps=1, f32_vectors=False):
+def batched_48x4_12_point_sources(reps=1, f32_vectors=False):
     """48^4, eps 0.25, kappa 0.125, c_SW 1.1, the 12 spin-colour point sources
     at the origin, to float64 true residual 1e-10, three ways on one GPU:
     one batched mixed-precision solve (float16-storage SAP, float32
@@ -184,7 +184,7 @@ def north_star_48x4(reps=1, f32_vectors=False):
 
 
 def c3(args):
-    out = north_star_48x4(reps=1, f32_vectors=True)
+    out = batched_48x4_12_point_sources(reps=1, f32_vectors=True)
     return {"config": {"workload": "48^4, eps 0.25, kappa 0.125, c_sw 1.1, 12 spin-colour point sources at the "
                                    "origin; batched float16-storage SAP + float32 BiCGStab + float64 "
                                    "correction to 1e-10 (device-side graph loop) vs 12 sequential mixed and "
