@@ -214,8 +214,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // block copies that lattice's descriptor (geometry, field pointers, kappa)
 // to shared memory, so the geometry is read from there rather than from
 // global memory on every index computation.
+template <int MODE>
 __global__ void __launch_bounds__(128, 4) dslash_batch_kernel(const BatchDesc* __restrict__ desc,
-                                                              const int* __restrict__ block_lat, int dagger) {
+                                                              const int* __restrict__ block_lat) {
   __shared__ BatchDesc sd;
   {
     const int i = __ldg(block_lat + blockIdx.x);
@@ -228,21 +229,17 @@ __global__ void __launch_bounds__(128, 4) dslash_batch_kernel(const BatchDesc* _
   if (gid >= sd.g.vol) return;
   const F32Spinor out{sd.out}, in{(float4*)sd.in};
   const CloverPtrF32 clov{sd.clov};
-  if (sd.u12) {  // this lattice's links as 12 reals (uniform over the block)
-    const LinkPtr12 U{sd.u12};
-    if (dagger) dslash_site<float, MODE_DDAG, true, LinkPtr12>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
-    else dslash_site<float, MODE_D, true, LinkPtr12>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
-  } else {
-    const LinkPtr<float> U{sd.u};
-    if (dagger) dslash_site<float, MODE_DDAG, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
-    else dslash_site<float, MODE_D, true>(sd.g, out, in, U, clov, sd.kappa, gid, 0);
-  }
+  if (sd.u12)  // this lattice's links as 12 reals (uniform over the block)
+    dslash_site<float, MODE, true, LinkPtr12>(sd.g, out, in, LinkPtr12{sd.u12}, clov, sd.kappa, gid, 0);
+  else
+    dslash_site<float, MODE, true>(sd.g, out, in, LinkPtr<float>{sd.u}, clov, sd.kappa, gid, 0);
 }
 
 void dslash_batch_launch(const BatchDesc* d_desc, const int* d_block_lat, long long total_blocks, int dagger,
                          cudaStream_t st) {
   QCD_REQUIRE(total_blocks < (1LL << 31), QCD_ERR_ARG, "batch too large for one launch");
-  dslash_batch_kernel<<<(unsigned)total_blocks, 128, 0, st>>>(d_desc, d_block_lat, dagger);
+  if (dagger) dslash_batch_kernel<MODE_DDAG><<<(unsigned)total_blocks, 128, 0, st>>>(d_desc, d_block_lat);
+  else dslash_batch_kernel<MODE_D><<<(unsigned)total_blocks, 128, 0, st>>>(d_desc, d_block_lat);
   check_launch();
 }
 
